@@ -1,0 +1,373 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: values the
+paper prints, closed forms, exact invariants, an independently written
+whole-array evaluation (tests/np_lbm.py), or brute force on tiny lattices.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import np_lbm
+from oracle import OracleProblem, feq_forcing, lattice_info
+from oracle.thermo import LatticeUnits, flash, maxwell
+from oracle.workloads import slab, two_phase_pressure
+from paper_2306_10652_gb300 import synth
+
+GOLDEN = __import__("os").path.join(__import__("os").path.dirname(__file__), "golden")
+
+
+def load_components():
+    rows = {}
+    for line in open(f"{GOLDEN}/components.txt"):
+        if line.startswith("#") or not line.strip():
+            continue
+        name, pc, Tc, om, M = line.split()
+        rows[name] = (float(pc), float(Tc), float(om), float(M))
+    return rows
+
+
+def load_vle():
+    out = []
+    for line in open(f"{GOLDEN}/vle_cases.txt"):
+        if line.startswith("#") or not line.strip():
+            continue
+        f = line.split()
+        xs = [float(v) for v in f[5:] if v != "-"]
+        out.append((int(f[0]), float(f[1]), float(f[2]), f[3], float(f[4]), np.array(xs)))
+    return out
+
+
+def synthetic_problem(seed, nc, lattice=0, shape=(1, 4, 4), Tfac=0.75, **kw):
+    """Seeded PR mixture at T = Tfac * min Tc (Tfac < 1) or Tfac * max Tc (Tfac > 1)."""
+    c = synth.pr_components(seed, nc)
+    P0 = OracleProblem(lattice, shape[2], shape[1], shape[0], c["a"], c["b"], c["omega"], c["kij"], T=1.0)
+    Tc = P0.critical_temperatures()
+    T = Tfac * (Tc.min() if Tfac < 1 else Tc.max())
+    return OracleProblem(lattice, shape[2], shape[1], shape[0], c["a"], c["b"], c["omega"], c["kij"],
+                         T=T, **kw)
+
+
+# ---------------------------------------------------------------------------
+# lattice tables (standard D2Q9 / D3Q19 isotropy up to fourth order)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("lattice", [0, 1])
+def test_lattice_isotropy(lattice):
+    D, Q, e, w = lattice_info(lattice)
+    cs2 = 1.0 / 3.0
+    assert abs(w.sum() - 1.0) < 1e-15
+    assert np.allclose(w @ e, 0.0, atol=1e-16)
+    M2 = np.einsum("a,ai,aj->ij", w, e, e)
+    assert np.allclose(M2[:D, :D], cs2 * np.eye(D), atol=1e-15)
+    M4 = np.einsum("a,ai,aj,ak,al->ijkl", w, e, e, e, e)[:D, :D, :D, :D]
+    I = np.eye(D)
+    iso = cs2 ** 2 * (np.einsum("ij,kl->ijkl", I, I) + np.einsum("ik,jl->ijkl", I, I)
+                      + np.einsum("il,jk->ijkl", I, I))
+    assert np.allclose(M4, iso, atol=1e-15)
+    # every velocity has its opposite
+    for a in range(Q):
+        assert any((e[b] == -e[a]).all() for b in range(Q))
+
+
+# ---------------------------------------------------------------------------
+# thermodynamics (Sec. 2.3)
+# ---------------------------------------------------------------------------
+def helmholtz(P: OracleProblem, rhom):
+    """Helmholtz free-energy density of the PR mixture (ideal + residual).
+
+    a_H = RT sum_i r_i (ln r_i - 1) - RT r ln(1 - B)
+          - (sum_ij r_i r_j A_ij)/(2 sqrt2 sum_i b_i r_i) ln[(1+(1+s2)B)/(1+(1-s2)B)],
+    B = sum_i b_i r_i.  Its pressure r^2 d(a/r)/dr is Eq. (9); its
+    derivatives are the chemical potentials whose fugacity form is Eq. (12).
+    """
+    RT = P.R * P.T
+    r = np.asarray(rhom, float)
+    aa = P.a * np_lbm.alpha(P.a, P.b, P.omega, P.T, P.R)
+    A = np.sqrt(np.outer(aa, aa)) * (1.0 - P.kij)
+    B = float(P.b @ r)
+    s2 = np.sqrt(2.0)
+    ideal = RT * float(np.sum(r * (np.log(r) - 1.0)))
+    rep = -RT * r.sum() * np.log(1.0 - B)
+    att = -float(r @ A @ r) / (2 * s2 * B) * np.log((1 + (1 + s2) * B) / (1 + (1 - s2) * B))
+    return ideal + rep + att
+
+
+def dA(P, r, i, h):
+    """Fourth-order central difference of helmholtz in rho~_i."""
+    def f(d):
+        rr = r.copy(); rr[i] += d
+        return helmholtz(P, rr)
+    return (-f(2 * h) + 8 * f(h) - 8 * f(-h) + f(-2 * h)) / (12 * h)
+
+
+@pytest.mark.parametrize("nc,seed", [(1, 0), (2, 1), (3, 2), (5, 3), (10, 4)])
+def test_lnf_is_helmholtz_derivative(nc, seed):
+    P = synthetic_problem(seed, nc, shape=(1, 1, 1))
+    RT = P.R * P.T
+    rng = np.random.default_rng(seed)
+    for trial in range(4):
+        z = rng.dirichlet(np.ones(nc))
+        rho = rng.uniform(0.2, 0.85) / float(z @ P.b)   # B from 0.2 to 0.85
+        r = z * rho
+        p, lnf = P.eos(r)
+        mu = np.array([dA(P, r, i, 1e-4 * r[i]) for i in range(nc)])
+        expect = RT * (lnf - np.log(RT))
+        assert np.allclose(mu, expect, rtol=1e-8, atol=1e-9 * RT), (mu, expect)
+        # Euler relation: p = sum_i rho~_i mu_i - a_H
+        assert abs(p - (float(r @ mu) - helmholtz(P, r))) < 1e-8 * max(abs(p), RT * rho * 1e-3)
+
+
+def test_ideal_gas_limit():
+    P = synthetic_problem(7, 4, shape=(1, 1, 1))
+    RT = P.R * P.T
+    r = np.array([1e-9, 2e-9, 3e-9, 4e-9])
+    p, lnf = P.eos(r)
+    assert abs(p / (r.sum() * RT) - 1.0) < 1e-7
+    assert np.allclose(lnf, np.log(r * RT), atol=1e-7)
+
+
+def test_alpha_is_one_at_critical_temperature():
+    c = synth.pr_components(3, 6, omega_range=(0.0, 1.0))
+    for i in range(6):
+        P = OracleProblem(0, 1, 1, 1, c["a"][i:i + 1], c["b"][i:i + 1], c["omega"][i:i + 1], T=1.0)
+        Tc = P.critical_temperatures()[0]
+        P = OracleProblem(0, 1, 1, 1, c["a"][i:i + 1], c["b"][i:i + 1], c["omega"][i:i + 1], T=Tc)
+        assert abs(P.alpha()[0] - 1.0) < 1e-14
+
+
+def test_printed_eq12_matches_where_p_positive():
+    """The oracle's cancelled form equals Eq. (12) as printed wherever p > 0."""
+    P = synthetic_problem(11, 4, shape=(1, 1, 1), Tfac=1.5)
+    rng = np.random.default_rng(5)
+    for _ in range(10):
+        z = rng.dirichlet(np.ones(4))
+        r = z * rng.uniform(0.05, 0.8) / float(z @ P.b)
+        p, lnf = P.eos(r)
+        p2, lnf2 = np_lbm.pr_fields(r.reshape(4, 1, 1, 1), P.a, P.b, P.omega, P.kij, P.T, P.R)
+        assert abs(p - p2.item()) < 1e-14 * abs(p) + 1e-16
+        assert np.allclose(lnf, lnf2.ravel(), rtol=0, atol=1e-13)
+
+
+def test_maxwell_reproduces_case1():
+    """Pure C1 at 177.24 K: the paper prints 55.43 / 284.87 kg/m^3 (Table III,
+    Case 1; error 2e-8 vs theory, Table IV) and 30.02 bar (Table II)."""
+    comp = load_components()
+    pc, Tc, om, M = comp["C1"]
+    lu = LatticeUnits([Tc], [pc], [om], [M])
+    P = lu.problem(177.24)
+    psat, rV, rL = maxwell(P)
+    case1 = [r for r in load_vle() if r[0] == 1]
+    rhoV = lu.mass_density_kg_m3([rV])
+    rhoL = lu.mass_density_kg_m3([rL])
+    exp_V = [r[4] for r in case1 if r[3] == "V"][0]
+    exp_L = [r[4] for r in case1 if r[3] == "L"][0]
+    # R = 8.314462618 is a reading (the paper prints none): 5e-4 covers it
+    assert abs(rhoV / exp_V - 1) < 5e-4
+    assert abs(rhoL / exp_L - 1) < 5e-4
+    assert abs(lu.p_to_bar(psat) / 30.02 - 1) < 1e-3
+    # equal fugacity and pressure at the solution
+    pV, fV = P.eos([rV]); pL, fL = P.eos([rL])
+    assert abs(pV / pL - 1) < 1e-12 and abs(fV[0] - fL[0]) < 1e-12
+
+
+def test_flash_reproduces_cases_2_to_6():
+    """Flash at the initial (T, p) of Table II vs the LBM results of Table III.
+    The paper's own flash used an unprinted updated pressure, so the pin is
+    loose: 1.5 % in phase density, 0.006 absolute in mole fraction."""
+    comp = load_components()
+    names = ["C1", "C2", "C3", "C4", "C5", "C6"]
+    vle = load_vle()
+    for case in range(2, 7):
+        rows = [r for r in vle if r[0] == case]
+        T, p = rows[0][1], rows[0][2]
+        sel = [comp[n] for n in names[:case]]
+        lu = LatticeUnits([s[1] for s in sel], [s[0] for s in sel], [s[2] for s in sel],
+                          [s[3] for s in sel])
+        P = lu.problem(T)
+        res = flash(P, lu.p(p), np.ones(case) / case)
+        assert res is not None and res.residual < 1e-12
+        for (_, _, _, ph, rho_kg, xs) in rows:
+            rhoi = res.rhoi_V if ph == "V" else res.rhoi_L
+            comp_x = res.y if ph == "V" else res.x
+            assert abs(lu.mass_density_kg_m3(rhoi) / rho_kg - 1) < 0.015, (case, ph)
+            assert np.max(np.abs(comp_x - xs)) < 0.006, (case, ph, comp_x, xs)
+
+
+# ---------------------------------------------------------------------------
+# equilibrium and forcing moments (Eq. 1b, 1c)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("lattice", [0, 1])
+def test_feq_forcing_moments(lattice):
+    D, Q, e, w = lattice_info(lattice)
+    e = e[:, :D].astype(float)
+    cs2 = 1.0 / 3.0
+    rng = np.random.default_rng(lattice)
+    for _ in range(5):
+        rho = rng.uniform(0.1, 3.0)
+        u = rng.uniform(-0.1, 0.1, D)
+        F = rng.uniform(-0.01, 0.01, D)
+        G = rng.uniform(-0.5, 0.5, D)
+        geq, Fa = feq_forcing(lattice, rho, u, F, G)
+        assert abs(geq.sum() - rho) < 1e-14
+        assert np.allclose(e.T @ geq, rho * u, atol=1e-15)
+        assert np.allclose(np.einsum("a,ai,aj->ij", geq, e, e), rho * np.outer(u, u), atol=1e-15)
+        assert abs(Fa.sum()) < 1e-16
+        assert np.allclose(e.T @ Fa, F, atol=1e-16)
+        M2 = np.einsum("a,ai,aj->ij", Fa, e, e)
+        expect = (np.outer(F, u) + np.outer(u, F)
+                  + cs2 * (np.outer(u, G) + np.outer(G, u) + float(u @ G) * np.eye(D)))
+        assert np.allclose(M2, expect, atol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# discrete operators: exact on low-order polynomials away from the wrap
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("lattice,shape", [(0, (1, 9, 11)), (1, (7, 8, 9))])
+def test_stencils_exact_on_polynomials(lattice, shape):
+    P = OracleProblem(lattice, shape[2], shape[1], shape[0], [0.04], [0.1], [0.1], T=0.05)
+    z, y, x = np.meshgrid(*[np.arange(n, dtype=float) for n in shape], indexing="ij")
+    lin = 0.3 * x - 0.7 * y + 0.2 * z + 1.0
+    quad = x * x + 2 * y * y - 0.5 * x * y + (3 * z * z + x * z if lattice == 1 else 0)
+    G = P.gradient(lin)
+    L = P.laplacian(quad)
+    inner = (slice(1, -1) if shape[0] > 2 else slice(None), slice(1, -1), slice(1, -1))
+    assert np.allclose(G[0][inner], 0.3) and np.allclose(G[1][inner], -0.7)
+    if lattice == 1:
+        assert np.allclose(G[2][inner], 0.2)
+    expect = 2 + 4 + (6 if lattice == 1 else 0)
+    assert np.allclose(L[inner], expect)
+
+
+# ---------------------------------------------------------------------------
+# the step: brute force, invariants and equivariances
+# ---------------------------------------------------------------------------
+def random_g(P, seed, lo=0.05, hi=0.6, uamp=2e-3):
+    nc = P.nc
+    scale = 1.0 / np.asarray(P.b)[:, None, None, None] / nc
+    rho = synth.random_state(seed, nc, P.shape, lo, hi) * scale
+    u = synth.random_velocity(seed, P.D, P.shape, uamp)
+    return P.init_equilibrium(rho, u)
+
+
+@pytest.mark.parametrize("lattice,shape,nc,Tfac,seed", [
+    (0, (1, 4, 4), 2, 1.3, 0),
+    (0, (1, 3, 5), 3, 1.3, 1),
+    (0, (1, 4, 4), 2, 0.8, 2),
+    (1, (3, 4, 5), 2, 1.3, 3),
+])
+def test_step_matches_independent_numpy(lattice, shape, nc, Tfac, seed):
+    P = synthetic_problem(seed, nc, lattice, shape, Tfac=Tfac, tau=0.8,
+                          M=synth.uniform(seed, 0.5, 2.0, nc))
+    lo, hi = (0.05, 0.6) if Tfac > 1 else (0.01, 0.08)
+    g = random_g(P, seed, lo, hi)
+    g1 = P.step(g, 1)
+    # the numpy helper keeps its own velocity ordering: map by matching vectors
+    _, _, e_orc, _ = lattice_info(lattice)
+    _, e_np, _ = np_lbm.d2q9() if lattice == 0 else np_lbm.d3q19()
+    to_np = [int(np.where((e_orc == v).all(axis=1))[0][0]) for v in e_np]
+    g2n = np_lbm.step(g[:, to_np], lattice, P.a, P.b, P.omega, P.kij, P.M, P.T, P.tau)
+    g2 = np.empty_like(g2n)
+    g2[:, to_np] = g2n
+    scale = np.abs(g).max(axis=(1, 2, 3, 4), keepdims=True)
+    assert np.max(np.abs(g1 - g2) / scale) < 1e-13
+
+
+def test_mass_conservation_and_fixed_point():
+    P = synthetic_problem(4, 3, 0, (1, 16, 24), Tfac=0.75)
+    g = random_g(P, 4, 0.01, 0.08)
+    m0 = P.mass(g)
+    g1 = P.step(g, 20)
+    assert np.allclose(P.mass(g1), m0, rtol=1e-13)
+    # uniform rest state is a fixed point bit for bit
+    rho = np.ones((3,) + P.shape) * (0.3 / P.b[:, None, None, None] / 3)
+    gu = P.init_equilibrium(rho)
+    assert np.array_equal(P.step(gu, 3), gu)
+
+
+def test_translation_reflection_permutation():
+    P = synthetic_problem(5, 3, 0, (1, 6, 8), Tfac=0.8)
+    g = random_g(P, 5, 0.01, 0.08)
+    g1 = P.step(g, 2)
+    # translation
+    gt = np.roll(g, (2, 3), axis=(-2, -1))
+    assert np.allclose(P.step(gt, 2), np.roll(g1, (2, 3), axis=(-2, -1)), rtol=0, atol=1e-14)
+    # reflection x -> -x: mirror the grid and swap directions with e_x -> -e_x
+    D, Q, e, w = lattice_info(0)
+    perm = [int(np.where((e == e[a] * np.array([-1, 1, 1])).all(axis=1))[0][0]) for a in range(Q)]
+    def mirror(h):
+        return np.flip(h[:, perm], axis=-1).copy()
+    assert np.allclose(P.step(mirror(g), 2), mirror(g1), rtol=0, atol=1e-14)
+    # component permutation
+    pi = [2, 0, 1]
+    Pp = OracleProblem(0, P.nx, P.ny, P.nz, P.a[pi], P.b[pi], P.omega[pi], P.kij[np.ix_(pi, pi)],
+                       P.T, P.tau, kappa_ref_index=pi.index(0))
+    assert np.allclose(Pp.step(g[pi], 2), g1[pi], rtol=0, atol=1e-14)
+
+
+def test_identical_components_reduce_to_one():
+    """Two copies of one fluid at a uniform split ratio evolve like the pure fluid."""
+    c = synth.pr_components(8, 1)
+    P1 = OracleProblem(0, 12, 6, 1, c["a"], c["b"], c["omega"], T=1.0)
+    T = 0.8 * P1.critical_temperatures()[0]
+    P1 = OracleProblem(0, 12, 6, 1, c["a"], c["b"], c["omega"], T=T)
+    P2 = OracleProblem(0, 12, 6, 1, np.repeat(c["a"], 2), np.repeat(c["b"], 2),
+                       np.repeat(c["omega"], 2), np.zeros((2, 2)), T=T)
+    rho = synth.random_state(8, 1, P1.shape, 0.5, 7.0)
+    g1 = P1.init_equilibrium(rho)
+    g2 = P2.init_equilibrium(np.concatenate([0.3 * rho, 0.7 * rho]))
+    for _ in range(3):
+        g1 = P1.step(g1, 5)
+        g2 = P2.step(g2, 5)
+        assert np.allclose(g2.sum(axis=0), g1[0], rtol=0, atol=1e-12 * np.abs(g1).max())
+        assert np.allclose(g2[0], 0.3 * g1[0], rtol=0, atol=1e-12 * np.abs(g1).max())
+
+
+@pytest.mark.slow
+def test_flat_interface_single_component_reaches_maxwell():
+    """Nc = 1 flat interface (Eq. 15 start, S_V = 0.5, W = 4): the LBM bulk
+    phases converge to the Maxwell coexistence densities and to equal
+    fugacity (the paper reports 2e-8 relative error for Case 1, Table IV).
+
+    With the central-difference gradient an even/odd (checkerboard) mode of
+    the chemical potential is not damped; the sharp initial profile excites
+    it at the 1e-5 level at T_r = 0.93, so the pin tolerance is 2e-4."""
+    c = synth.pr_components(9, 1)
+    nx = 128
+    P = OracleProblem(0, nx, 1, 1, c["a"], c["b"], c["omega"], T=1.0)
+    P = OracleProblem(0, nx, 1, 1, c["a"], c["b"], c["omega"], T=0.93 * P.critical_temperatures()[0])
+    psat, rV, rL = maxwell(P)
+    g = P.init_equilibrium(slab(np.array([rV]), np.array([rL]), nx)[:, None, None, :])
+    g = P.step(g, 12000)
+    m = P.moments(g)
+    r = m["rho"][0, 0, 0]
+    assert abs(r[nx // 2] / rL - 1) < 2e-4 and abs(r[0] / rV - 1) < 2e-4
+    lnf = m["lnf"][0, 0, 0]
+    assert abs(lnf[nx // 2] - lnf[0]) < 1e-4
+    assert np.abs(m["u"]).max() < 1e-7
+
+
+@pytest.mark.slow
+def test_flat_interface_binary_reaches_flash():
+    """Binary flat interface at S_V = 0.5: bulk compositions converge to the
+    flash at the LBM's own pressure and overall composition (Sec. 3.2)."""
+    c = synth.pr_components(0, 2)
+    nx = 64
+    P = OracleProblem(0, nx, 1, 1, c["a"], c["b"], c["omega"], c["kij"], T=1.0)
+    T = 0.85 * P.critical_temperatures().mean()
+    P = OracleProblem(0, nx, 1, 1, c["a"], c["b"], c["omega"], c["kij"], T=T)
+    z = np.array([0.5, 0.5])
+    p, fl = two_phase_pressure(P, z, 0.5)
+    g = P.init_equilibrium(slab(fl.rhoi_V, fl.rhoi_L, nx)[:, None, None, :])
+    g = P.step(g, 30000)
+    m = P.moments(g)
+    rr = m["rho"][:, 0, 0]
+    xL = rr[:, nx // 2] / rr[:, nx // 2].sum()
+    xV = rr[:, 0] / rr[:, 0].sum()
+    pm = 0.5 * (m["p"][0, 0, nx // 2] + m["p"][0, 0, 0])
+    f2 = flash(P, pm, rr.sum(axis=1) / rr.sum())
+    # the paper's own LBM-vs-flash errors reach 0.264909 % (Table IV); the
+    # pin allows twice that, relative, in every mole fraction
+    assert np.max(np.abs(xL / f2.x - 1)) < 5e-3 and np.max(np.abs(xV / f2.y - 1)) < 5e-3
+    # iso-fugacity between the phase centres (same sublattice: x = 0 and nx/2)
+    assert np.max(np.abs(m["lnf"][:, 0, 0, nx // 2] - m["lnf"][:, 0, 0, 0])) < 5e-5
