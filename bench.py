@@ -1,0 +1,304 @@
+"""Benchmark of the per-step multicomponent LBM hot path on GB300.
+
+Workload (headline): spinodal decomposition, D2Q9 2048 x 2048 periodic,
+Nc = 10 seeded Peng-Robinson components (parameters and the uniform state
+written by oracle/make_workloads.py into paper_2306_10652_gb300/workloads/),
++-1 % seeded multiplicative density noise.  A step is one full update of
+all populations (pull of the paper's Eq. 1a, Eqs. 1b/1c/5/9-12) plus the
+on-device per-component mass reduction.
+
+Metric: Nc-weighted lattice updates per second, Nc * nodes * steps / s / 1e9
+("Nc*GLUPS"), whole job.  Roofline: algorithmic bytes per node-step
+2 * Q * Nc * bytes_per_population (each population read and written once).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+       [--nc NC] [--precision fp32dev|fp64] [--schedule auto|threepass|fused]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD_FILE = os.path.join(ROOT, "paper_2306_10652_gb300", "workloads", "spinodal_2048.json")
+METRIC = "Nc·GLUPS"
+HBM_FALLBACK_GBS = 6800.0
+
+
+def load_case(nc):
+    d = json.load(open(WORKLOAD_FILE))
+    case = [c for c in d["cases"] if c["nc"] == nc][0]
+    return d, case
+
+
+def initial_density(d, case, nx, ny, seed=2):
+    """rho_i = z_i rho~ M_i (M_i = 1) times the seeded multiplicative noise."""
+    from paper_2306_10652_gb300 import synth
+    z = np.asarray(case["z"])
+    rho = z[:, None, None] * case["rho_molar_total"] * np.ones((1, ny, nx))
+    return (rho * synth.multiplicative_noise(seed, rho.shape, 0.01))[:, None]  # [nc, 1, ny, nx]
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": HBM_FALLBACK_GBS}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.out.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, fl in rows for k, v in enumerate(fl) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2306_10652_gb300 import lbmfug
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    d, case = load_case(args.nc)
+    nx, ny = d["nx"], d["ny"]
+    nc = case["nc"]
+    prec = {"fp64": lbmfug.LBM_FP64, "fp32dev": lbmfug.LBM_FP32DEV}[args.precision]
+    sched = {"auto": lbmfug.LBM_SCHED_AUTO, "threepass": lbmfug.LBM_SCHED_THREEPASS,
+             "fused": lbmfug.LBM_SCHED_FUSED}[args.schedule]
+    rho = initial_density(d, case, nx, ny)
+    stream = torch.cuda.Stream()
+    kw = dict(precision=prec, schedule=sched, kappa_ref=case["kappa_ref"], stream=stream.cuda_stream,
+              monitor_every=1)
+    prob = lbmfug.Problem(0, nx, ny, 1, case["a"], case["b"], case["omega"],
+                          np.asarray(case["kij"]), case["T"], case["tau"], **kw)
+    d_rho = torch.from_numpy(rho.reshape(-1)).to(f"cuda:{local}")
+    prob.init_fields_device(d_rho)
+    del d_rho
+    prob.step(args.warmup)
+    prob.synchronize()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = prob.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        prob.step(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+    torch.cuda.synchronize()
+    launches = prob.launch_count() - l0
+    ms = e0.elapsed_time(e1)
+    mass, at, nonfinite = prob.monitor()
+    if ws > 1:
+        t = torch.tensor([ms], device=f"cuda:{local}", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    prob.close()
+    N = nx * ny
+    node_steps = N * args.steps * ws
+    value = nc * node_steps / (ms * 1e-3) / 1e9
+    spop = 8 if prec == lbmfug.LBM_FP64 else 4
+    alg_bytes_per_launch = 2 * 9 * nc * spop * N
+    step_ms = ms / args.steps
+    pk, pk_kind = peaks()
+    achieved = alg_bytes_per_launch / (step_ms * 1e-3) / 1e9  # GB/s, whole step per launch
+    e2e = run_e2e(args, lbmfug, case, rho, nx, ny, prec, sched, local) if rank == 0 else None
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return None
+    cpu = cpu_baseline(case, nx, ny, rho) if (ws == 1 and not args.no_cpu_baseline) else None
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == lbmfug.LBM_FP32DEV else "f64",
+        "data": "synthetic (seeded PR mixture, uniform state in the spinodal region + 1% noise)",
+        "config": {"workload": f"spinodal decomposition D2Q9 {nx}x{ny} periodic, Nc={nc}",
+                   "lattice": "D2Q9", "nx": nx, "ny": ny, "nc": nc,
+                   "precision": args.precision, "schedule": args.schedule,
+                   "parallelism": f"replicas{ws}" if ws > 1 else "single",
+                   "l2": "inputs larger than L2 (populations %.2f GB per buffer)" % (9 * nc * spop * N / 1e9)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                     "peak_kind": pk_kind, "algorithmic_bytes_per_node_step": 2 * 9 * nc * spop},
+        "gpu_launches": launches,
+        "mass_monitor": {"at_step": at, "nonfinite": nonfinite,
+                         "mass": None if mass is None else [float(v) for v in mass]},
+        "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+    }
+    if ws > 1:
+        dist.destroy_process_group()
+    return line
+
+
+def run_e2e(args, lbmfug, case, rho, nx, ny, prec, sched, local):
+    """Same metric through the public C ABI with host buffers: pinned-host
+    densities in (H2D inside lbm_init_fields), K steps, densities out (D2H)."""
+    import torch
+    N = nx * ny
+    nc = case["nc"]
+    h_in = torch.empty(nc * N, dtype=torch.float64, pin_memory=True).numpy()
+    h_in[:] = rho.reshape(-1)
+    h_out = torch.empty(nc * N, dtype=torch.float64, pin_memory=True).numpy()
+    prob = lbmfug.Problem(0, nx, ny, 1, case["a"], case["b"], case["omega"], np.asarray(case["kij"]),
+                          case["T"], case["tau"], precision=prec, schedule=sched,
+                          kappa_ref=case["kappa_ref"], monitor_every=1)
+    prob.init_fields(h_in)          # first call allocates; not timed
+    prob.synchronize()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    prob.init_fields(h_in)
+    prob.step(args.steps)
+    out = prob.moments(("rho",))["rho"]
+    h_out[:] = out.reshape(-1)
+    t1 = time.perf_counter()
+    prob.close()
+    wall = t1 - t0
+    return {"value": nc * N * args.steps / wall / 1e9, "unit": METRIC,
+            "h2d_bytes_per_step": nc * N * 8 / args.steps, "d2h_bytes_per_step": nc * N * 8 / args.steps,
+            "wall_s": wall}
+
+
+def oracle_sample(case, nx, ny, rho, crop=64, steps=4):
+    """Time the CPU oracle on a crop of the workload (bounded sample)."""
+    from oracle import OracleProblem
+    nc = case["nc"]
+    P = OracleProblem(0, crop, crop, 1, case["a"], case["b"], case["omega"], np.asarray(case["kij"]),
+                      T=case["T"], tau=case["tau"], kappa_ref=case["kappa_ref"])
+    g = P.init_equilibrium(np.ascontiguousarray(rho[:, :, :crop, :crop]))
+    t0 = time.perf_counter()
+    P.step(g, steps)
+    dt = time.perf_counter() - t0
+    return nc * crop * crop * steps / dt / 1e9, dt
+
+
+def cpu_baseline(case, nx, ny, rho, target_s=12.0):
+    crop, steps = 64, 2
+    v, dt = oracle_sample(case, nx, ny, rho, crop, steps)
+    steps = max(2, min(400, int(steps * target_s / max(dt, 1e-3))))
+    v, dt = oracle_sample(case, nx, ny, rho, crop, steps)
+    return {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"{crop}x{crop} crop of the workload, {steps} steps ({dt:.1f} s), single thread"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return None
+    d, case = load_case(args.nc)
+    nx, ny = d["nx"], d["ny"]
+    rho = initial_density(d, case, 64, 64)
+    crop = 64
+    for _ in range(args.warmup):
+        oracle_sample(case, nx, ny, rho, crop, 1)
+    per_step_s = max(0.5, 60.0 / max(args.steps, 1))
+    _, dt1 = oracle_sample(case, nx, ny, rho, crop, 1)
+    inner = max(1, int(per_step_s / max(dt1, 1e-3)))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_sample(case, nx, ny, rho, crop, inner)
+    wall = time.perf_counter() - t0
+    nc = case["nc"]
+    value = nc * crop * crop * inner * args.steps / wall / 1e9
+    sample = f"{crop}x{crop} crop of the workload, {inner} oracle steps per bench step, single thread"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"spinodal decomposition D2Q9 {nx}x{ny} periodic, Nc={nc}",
+                                            "lattice": "D2Q9", "nx": nx, "ny": ny, "nc": nc},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--nc", type=int, default=10)
+    ap.add_argument("--precision", default="fp32dev", choices=["fp32dev", "fp64"])
+    ap.add_argument("--schedule", default="auto", choices=["auto", "threepass", "fused"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    line = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * lbmfug.h -- C ABI of the GB300-native fugacity-based multicomponent lattice
+ * Boltzmann library (Soomro & Ayala, "Unrestricted component count in
+ * multiphase lattice Boltzmann: a fugacity-based approach", arXiv 2306.10652).
+ *
+ * One time step updates, at every node of a periodic D2Q9 or D3Q19 lattice,
+ * the populations of all Nc components:
+ *   Eq. (1a)  g_{a,i}(r + e_a, t + 1) = g_{a,i} - (g_{a,i} - g^eq_{a,i})/tau
+ *                                      + (1 - 1/(2 tau)) F_{a,i}
+ *   Eq. (1b)  well-balanced equilibrium with rho_i^c = 0
+ *   Eq. (1c)  well-balanced forcing term
+ *   Eq. (5)   F_i = -rho~_i RT grad ln f_i + rho~_i sum_j grad(sqrt(k_i k_j) lap rho~_j)
+ *   Eqs. (9)-(12)  Peng-Robinson mixture pressure and fugacities with the
+ *             van der Waals mixing rules and binary parameters delta_ij
+ *   Eq. (6)   kappa_i = kappa_ref a_i / a_ref
+ * Readings of what the paper leaves open (shared velocity, discrete
+ * gradient/Laplacian, initial populations) are those of the library's design
+ * notes: u = (sum e g + F/2)/rho, isotropic lattice stencils, g = g^eq(rho, u).
+ *
+ * Conventions
+ *  - Every call returns an int status (LBM_OK = 0 or a negative LBM_E*);
+ *    nothing else crosses the ABI (no exceptions, no aborts).
+ *  - Host arrays are owned by the caller and copied; device memory of a
+ *    problem is owned by the library (or by the caller's allocator hooks).
+ *  - Field layout: component-major, then z, y, x with x fastest:
+ *    rho[i][z][y][x], u[d][z][y][x].  Populations (get/set_state) are
+ *    g[i][a][z][y][x] in the post-streaming convention of Eq. (1a), with the
+ *    velocity order of lbm_lattice_velocities().
+ *  - A handle is not thread-safe; separate handles are independent.
+ *  - Work is enqueued on the handle's CUDA stream; calls that return host
+ *    data synchronise that stream.
+ */
+#ifndef LBMFUG_H
+#define LBMFUG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_MAX_NC 16
+
+enum lbm_lattice { LBM_D2Q9 = 0, LBM_D3Q19 = 1 };
+
+/* Population storage.  LBM_FP64 stores g in binary64 and computes every step
+ * in binary64 (the plain path).  LBM_FP32DEV stores g_{a,i} - delta_{a0} rhobar_i
+ * (deviation from the rest equilibrium of the mean density) in binary32, with
+ * the collision in binary32 and the thermodynamics in binary64. */
+enum lbm_precision { LBM_FP64 = 0, LBM_FP32DEV = 1 };
+
+/* Kernel schedule: LBM_SCHED_AUTO picks the fused single-pass kernel where it
+ * exists (D2Q9) and the three-pass kernels otherwise. */
+enum lbm_schedule { LBM_SCHED_AUTO = 0, LBM_SCHED_THREEPASS = 1, LBM_SCHED_FUSED = 2 };
+
+enum lbm_status {
+    LBM_OK = 0,
+    LBM_EINVAL = -1,     /* invalid argument or parameter */
+    LBM_ENOMEM = -2,     /* device or host allocation failed */
+    LBM_ECUDA = -3,      /* CUDA runtime error (launch, copy, device) */
+    LBM_ENONFINITE = -4, /* a non-finite density was detected */
+    LBM_ETIMEOUT = -5,   /* a bounded device wait ran out */
+    LBM_ESTATE = -6,     /* call not valid in the handle's current state */
+    LBM_ENOTSUP = -7     /* combination not supported by this build */
+};
+
+typedef struct lbm_problem lbm_problem;
+
+/* Allocation hooks: alloc returns device memory of `bytes` bytes on the
+ * current device, free releases it.  ctx is passed through unchanged. */
+typedef void *(*lbm_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*lbm_free_fn)(void *ptr, size_t bytes, void *ctx);
+
+typedef struct lbm_options {
+    int precision;        /* enum lbm_precision, default LBM_FP64 */
+    int schedule;         /* enum lbm_schedule, default LBM_SCHED_AUTO */
+    double kappa_ref;     /* interface parameter of the reference component, default 0.02 (Sec. 3) */
+    int kappa_ref_index;  /* reference component for Eq. (6), default 0 */
+    const double *M;      /* molar masses M_i (rho_i = M_i rho~_i); NULL = all 1 */
+    double R;             /* gas constant in lattice units, default 1 (Sec. 3.1) */
+    void *stream;         /* cudaStream_t to enqueue on; NULL = a stream the library creates */
+    int monitor_every;    /* > 0: every that many steps lbm_step also reduces the
+                             per-component mass of the new state on the device
+                             (read with lbm_monitor); 0 = off (default) */
+    lbm_alloc_fn alloc;   /* NULL = cudaMalloc */
+    lbm_free_fn free;     /* must be set together with alloc */
+    void *alloc_ctx;
+} lbm_options;
+
+/* Fill *opt with the defaults listed above. */
+int lbm_options_default(lbm_options *opt);
+
+/*
+ * Create a problem: lattice LBM_D2Q9 (nz must be 1) or LBM_D3Q19, a periodic
+ * nx*ny*nz box, Nc in 1..LBM_MAX_NC components with PR attraction a_i > 0 and
+ * co-volume b_i > 0 in lattice units (Sec. 2.3), acentric factors omega_i,
+ * binary parameters kij (Nc*Nc row-major, symmetric, zero diagonal,
+ * |k_ij| < 1; NULL = all zero), temperature T > 0 and relaxation time
+ * tau > 0.5.  T_c,i is implied by a_i/b_i (Sec. 2.3).  Allocates nothing on
+ * the device until lbm_init_fields.  *out is NULL on failure.
+ */
+int lbm_create(lbm_problem **out, int lattice, int nx, int ny, int nz, int Nc,
+               const double *a, const double *b, const double *omega, const double *kij,
+               double T, double tau);
+
+/* Set options; valid only before the first lbm_init_fields / lbm_set_state.
+ * opt->M is copied. */
+int lbm_set_options(lbm_problem *p, const lbm_options *opt);
+
+/*
+ * Initialise the populations at the equilibrium of Eq. (1b) for the given
+ * mass densities rho[i][z][y][x] (> 0, finite) and velocity u[d][z][y][x]
+ * (NULL = fluid at rest).  Host pointers.  Resets the step counter.
+ */
+int lbm_init_fields(lbm_problem *p, const double *rho, const double *u);
+
+/* Same with device pointers (binary64, same layouts), enqueued on the handle's stream. */
+int lbm_init_fields_device(lbm_problem *p, const double *d_rho, const double *d_u);
+
+/* Advance n >= 0 time steps (asynchronous on the handle's stream).  Returns a
+ * launch error or a sticky earlier error. */
+int lbm_step(lbm_problem *p, long long n);
+
+/*
+ * Macroscopic fields of the current state into caller-owned host buffers
+ * (any may be NULL): rho[i][...] mass densities; u[d][...] the velocity of
+ * the forced step, (sum e g + F/2)/rho; p[...] the PR pressure of Eq. (9) at
+ * the local composition; lnf[i][...] ln f_i of Eq. (12).  Synchronises.
+ */
+int lbm_moments(lbm_problem *p, double *rho, double *u, double *pressure, double *lnf);
+
+/* Same into device buffers, enqueued on the handle's stream. */
+int lbm_moments_device(lbm_problem *p, double *d_rho, double *d_u, double *d_pressure,
+                       double *d_lnf);
+
+/*
+ * Per-component total mass sum_r rho_i(r) into mass[Nc] (host), summed in a
+ * fixed order (bitwise reproducible).  Returns LBM_ENONFINITE if any density
+ * is not finite.  Synchronises.
+ */
+int lbm_mass(lbm_problem *p, double *mass);
+
+/*
+ * Convergence monitor: max over nodes and components of
+ * |rho_i(t) - rho_i(t_snap)|, where t_snap is the state at the previous call
+ * (the first call only takes the snapshot and reports +inf).  Synchronises.
+ */
+int lbm_convergence(lbm_problem *p, double *max_abs_drho);
+
+/* Latest on-device mass reduction of lbm_step's monitor (see
+ * lbm_options.monitor_every) into mass[Nc] (host) and the step it was taken
+ * at; *nonfinite = 1 if a non-finite density was seen since the last
+ * lbm_init_fields.  Synchronises. */
+int lbm_monitor(lbm_problem *p, double *mass, long long *at_step, int *nonfinite);
+
+/* Number of kernels this handle has launched (every launch is counted). */
+int lbm_launch_count(const lbm_problem *p, long long *launches);
+
+/* Raw populations, binary64, layout g[i][a][z][y][x] (post-streaming).
+ * *bytes in: capacity of buf; out: bytes needed.  buf NULL = size query. */
+int lbm_get_state(lbm_problem *p, double *buf, size_t *bytes);
+int lbm_set_state(lbm_problem *p, const double *buf, size_t bytes);
+
+/* Steps taken since the last init/set_state. */
+int lbm_step_count(const lbm_problem *p, long long *steps);
+
+/* Wait for all work enqueued on the handle's stream. */
+int lbm_synchronize(lbm_problem *p);
+
+/* Release the handle and its device memory.  NULL-safe. */
+int lbm_destroy(lbm_problem *p);
+
+/* Lattice description: D, Q and the velocities e[Q][3] used by get/set_state. */
+int lbm_lattice_velocities(int lattice, int *D, int *Q, int *e);
+
+/* Static text for a status code. */
+const char *lbm_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBMFUG_H */

@@ -74,14 +74,42 @@ def droplet(rhoi_V, rhoi_L, nx, ny, R, W=4.0):
     return 0.5 * (rl + rv) - 0.5 * (rl - rv) * np.tanh(2 * d / W)
 
 
-def spinodal_point(P: OracleProblem, z, npts=400):
-    """Total molar density on the fixed-z line where the smallest stability
-    eigenvalue is most negative (None if the line never enters the spinodal)."""
+def spinodal_point(P: OracleProblem, z, npts=400, B_max=0.6):
+    """Total molar density on the fixed-z line, with b_m rho~ <= B_max, where
+    the smallest stability eigenvalue is most negative (None if that part of
+    the line never enters the spinodal).  B_max keeps the uniform state away
+    from the nearly incompressible liquid branch, whose sound speed the
+    lattice cannot carry."""
     z = np.asarray(z, float)
     bm = float(z @ P.b)
-    rhos = np.linspace(0.02, 0.95, npts) / bm
+    rhos = np.linspace(0.02, B_max, npts) / bm
     lam = np.array([min_stability_eigenvalue(P, z * r) for r in rhos])
     k = int(np.argmin(lam))
     if lam[k] >= 0:
         return None
     return float(rhos[k]), float(lam[k])
+
+
+def spinodal_temperature(make_problem, z, T_lo, T_hi, npts=160, tol=1e-6, B_max=0.6):
+    """Highest temperature at which the fixed-z line (b_m rho~ <= B_max)
+    enters the spinodal region (bisection on the sign of the most negative
+    stability eigenvalue).  ``make_problem(T)`` returns an OracleProblem at T."""
+    def deepest(T):
+        P = make_problem(T)
+        bm = float(np.asarray(z) @ P.b)
+        rhos = np.linspace(0.02, B_max, npts) / bm
+        return min(min_stability_eigenvalue(P, np.asarray(z) * r) for r in rhos)
+    if deepest(T_lo) >= 0:
+        return None
+    lo, hi = T_lo, T_hi
+    while deepest(hi) < 0:
+        lo, hi = hi, 2 * hi
+    for _ in range(100):
+        mid = 0.5 * (lo + hi)
+        if deepest(mid) < 0:
+            lo = mid
+        else:
+            hi = mid
+        if hi - lo < tol * hi:
+            break
+    return lo

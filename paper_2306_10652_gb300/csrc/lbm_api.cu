@@ -1,0 +1,614 @@
+// lbm_api.cu -- the C ABI declared in include/lbmfug.h.
+//
+// Owns the handle, validates arguments, turns the problem statement of the
+// paper (Sec. 2.3: a_i, b_i, omega_i, delta_ij, T; Sec. 2.1: tau; Sec. 2.2:
+// kappa_ref) into the per-problem constant block, manages device memory and
+// dispatches to the kernels.  No exception or abort crosses the ABI.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lbm_internal.h"
+#include "lbmfug.h"
+
+using namespace lbmfug;
+
+struct lbm_problem {
+    int lattice = 0, nx = 0, ny = 0, nz = 0, nc = 0, D = 0, Q = 0;
+    long long N = 0;
+    double a[kMaxNc] = {}, b[kMaxNc] = {}, omega[kMaxNc] = {}, kij[kMaxNc * kMaxNc] = {};
+    double T = 0, tau = 1;
+    double M[kMaxNc] = {};
+    lbm_options opt{};
+    Params P{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    bool allocated = false;
+    bool initialized = false;
+    long long steps = 0;
+    int sticky = LBM_OK;
+    bool fused = false;
+    FusedGeom geo{};
+    void *g[2] = {nullptr, nullptr};
+    void *rs[2] = {nullptr, nullptr};  // fused schedule: density state
+    int cur = 0;
+    ThreePassWork w{};
+    double *snap = nullptr;
+    bool have_snap = false;
+    long long launches = 0;
+    long long monitor_step = -1;
+    double *mon = nullptr;  // [nc] latest monitored mass
+    double *partials = nullptr;
+    double *res = nullptr;
+    double *mass_partials = nullptr;
+    int *flag = nullptr;
+    std::vector<void *> blocks;
+    std::vector<size_t> block_bytes;
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ECUDA; }
+
+int pstore_bytes(const lbm_problem *p) { return p->opt.precision == LBM_FP32DEV ? 4 : 8; }
+
+void *dev_alloc(lbm_problem *p, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    void *ptr = nullptr;
+    if (p->opt.alloc) {
+        ptr = p->opt.alloc(bytes, p->opt.alloc_ctx);
+    } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        ptr = nullptr;
+    }
+    if (ptr) {
+        p->blocks.push_back(ptr);
+        p->block_bytes.push_back(bytes);
+    }
+    return ptr;
+}
+
+void dev_free_all(lbm_problem *p)
+{
+    for (size_t k = 0; k < p->blocks.size(); ++k) {
+        if (p->opt.alloc && p->opt.free)
+            p->opt.free(p->blocks[k], p->block_bytes[k], p->opt.alloc_ctx);
+        else if (!p->opt.alloc)
+            cudaFree(p->blocks[k]);
+    }
+    p->blocks.clear();
+    p->block_bytes.clear();
+}
+
+// Sec. 2.3: alpha_i(omega_i, T_r), with T_c,i implied by a_i and b_i.
+double pr_alpha(double a, double b, double omega, double T, double R)
+{
+    const double Tc = (0.077796074 / 0.457235529) * a / (R * b);
+    const double Tr = T / Tc;
+    double m;
+    if (omega <= 0.49)
+        m = 0.374640 + 1.54226 * omega - 0.26992 * omega * omega;
+    else
+        m = 0.379642 + 1.48503 * omega - 0.164423 * omega * omega + 0.016666 * omega * omega * omega;
+    const double s = 1.0 + m * (1.0 - std::sqrt(Tr));
+    return s * s;
+}
+
+void build_params(lbm_problem *p)
+{
+    Params &P = p->P;
+    std::memset(&P, 0, sizeof(P));
+    P.nx = p->nx;
+    P.ny = p->ny;
+    P.nz = p->nz;
+    P.nc = p->nc;
+    P.N = p->N;
+    P.RT = p->opt.R * p->T;
+    P.lnRT = std::log(P.RT);
+    P.omega = 1.0 / p->tau;
+    double aa[kMaxNc];
+    const double aref = p->a[p->opt.kappa_ref_index];
+    for (int i = 0; i < p->nc; ++i) {
+        aa[i] = p->a[i] * pr_alpha(p->a[i], p->b[i], p->omega[i], p->T, p->opt.R);
+        P.b[i] = p->b[i];
+        P.invM[i] = 1.0 / p->M[i];
+        P.sqk[i] = std::sqrt(p->opt.kappa_ref * p->a[i] / aref);  // Eq. (6), Eq. (4)
+    }
+    for (int i = 0; i < p->nc; ++i)
+        for (int j = 0; j < p->nc; ++j)
+            P.A[i * kMaxNc + j] = std::sqrt(aa[i] * aa[j]) * (1.0 - p->kij[i * kMaxNc + j]);
+}
+
+int ensure_allocated(lbm_problem *p)
+{
+    if (p->allocated) return LBM_OK;
+    if (!p->stream) {
+        if (p->opt.stream) {
+            p->stream = (cudaStream_t)p->opt.stream;
+        } else {
+            if (cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking) != cudaSuccess)
+                return LBM_ECUDA;
+            p->own_stream = true;
+        }
+    }
+    build_params(p);
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int sched = p->opt.schedule;
+    const bool can_fuse = fused_supported(p->lattice, p->nc);
+    if (sched == LBM_SCHED_FUSED && !can_fuse) return LBM_ENOTSUP;
+    p->fused = can_fuse && sched != LBM_SCHED_THREEPASS;
+    const size_t sb = (size_t)pstore_bytes(p);
+    const size_t gb = (size_t)p->nc * p->Q * p->N * sb;
+    const size_t fb = (size_t)p->nc * p->N * sizeof(double);
+    p->g[0] = dev_alloc(p, gb);
+    p->g[1] = dev_alloc(p, gb);
+    p->w.rho = (double *)dev_alloc(p, fb);
+    p->w.lnf = (double *)dev_alloc(p, fb);
+    p->w.psi = (double *)dev_alloc(p, (size_t)p->N * sizeof(double));
+    p->w.lap = (double *)dev_alloc(p, (size_t)p->N * sizeof(double));
+    p->w.jm = (double *)dev_alloc(p, (size_t)p->D * p->N * sizeof(double));
+    p->partials = (double *)dev_alloc(p, (size_t)kReduceBlocks * p->nc * sizeof(double));
+    p->res = (double *)dev_alloc(p, 64 * sizeof(double));
+    p->flag = (int *)dev_alloc(p, 16);
+    p->mon = (double *)dev_alloc(p, kMaxNc * sizeof(double));
+    if (!p->mon || !p->g[0] || !p->g[1] || !p->w.rho || !p->w.lnf || !p->w.psi || !p->w.lap || !p->w.jm ||
+        !p->partials || !p->res || !p->flag)
+        return LBM_ENOMEM;
+    if (p->fused) {
+        p->geo = fused_geometry(p->opt.precision, p->nc, p->P, nsm);
+        const size_t rb = (size_t)p->nc * p->N * sb;
+        p->rs[0] = dev_alloc(p, rb);
+        p->rs[1] = dev_alloc(p, rb);
+        p->mass_partials =
+            (double *)dev_alloc(p, (size_t)p->geo.nstrips * p->geo.segs * p->nc * sizeof(double));
+        if (!p->rs[0] || !p->rs[1] || !p->mass_partials) return LBM_ENOMEM;
+    }
+    if (cudaMemsetAsync(p->flag, 0, 16, p->stream) != cudaSuccess) return LBM_ECUDA;
+    p->allocated = true;
+    return LBM_OK;
+}
+
+int finish_init(lbm_problem *p)
+{
+    p->cur = 0;
+    p->steps = 0;
+    p->have_snap = false;
+    p->monitor_step = -1;
+    if (cudaMemsetAsync(p->flag, 0, 16, p->stream) != cudaSuccess) return LBM_ECUDA;
+    if (p->fused) {
+        int e = launch_fused_density(p->opt.precision, p->nc, p->P, p->g[0], p->rs[0], p->stream);
+        if (e) return LBM_ECUDA;
+        p->launches += 1;
+    }
+    p->initialized = true;
+    p->sticky = LBM_OK;
+    return cuda_status(cudaGetLastError());
+}
+
+// mean density per component over the field (deviation storage reference)
+int set_rhobar(lbm_problem *p, const double *d_rho)
+{
+    if (p->opt.precision != LBM_FP32DEV) return LBM_OK;
+    int e = launch_mass(p->nc, p->N, d_rho, p->partials, p->res, p->flag, p->stream);
+    if (e) return LBM_ECUDA;
+    double m[kMaxNc];
+    if (cudaMemcpyAsync(m, p->res, p->nc * sizeof(double), cudaMemcpyDeviceToHost, p->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(p->stream) != cudaSuccess)
+        return LBM_ECUDA;
+    for (int i = 0; i < p->nc; ++i) p->P.rhobar[i] = m[i] / (double)p->N;
+    return LBM_OK;
+}
+
+int check_flag(lbm_problem *p)
+{
+    int f = 0;
+    if (cudaMemcpyAsync(&f, p->flag, sizeof(int), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+        cudaStreamSynchronize(p->stream) != cudaSuccess)
+        return LBM_ECUDA;
+    return f ? LBM_ENONFINITE : LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_options_default(lbm_options *opt)
+{
+    if (!opt) return LBM_EINVAL;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = LBM_FP64;
+    opt->schedule = LBM_SCHED_AUTO;
+    opt->kappa_ref = 0.02;
+    opt->kappa_ref_index = 0;
+    opt->M = nullptr;
+    opt->R = 1.0;
+    return LBM_OK;
+}
+
+int lbm_create(lbm_problem **out, int lattice, int nx, int ny, int nz, int Nc, const double *a,
+               const double *b, const double *omega, const double *kij, double T, double tau)
+{
+    if (!out) return LBM_EINVAL;
+    *out = nullptr;
+    if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19) return LBM_EINVAL;
+    if (nx < 1 || ny < 1 || nz < 1 || (lattice == LBM_D2Q9 && nz != 1)) return LBM_EINVAL;
+    if (Nc < 1 || Nc > LBM_MAX_NC || !a || !b || !omega) return LBM_EINVAL;
+    if (!(T > 0.0) || !std::isfinite(T) || !(tau > 0.5) || !std::isfinite(tau)) return LBM_EINVAL;
+    if ((double)nx * ny * nz > 4.0e9) return LBM_EINVAL;
+    for (int i = 0; i < Nc; ++i) {
+        if (!(a[i] > 0.0) || !(b[i] > 0.0) || !std::isfinite(a[i]) || !std::isfinite(b[i]) ||
+            !std::isfinite(omega[i]))
+            return LBM_EINVAL;
+        if (kij) {
+            if (kij[i * Nc + i] != 0.0) return LBM_EINVAL;
+            for (int j = 0; j < Nc; ++j) {
+                const double k = kij[i * Nc + j];
+                if (!std::isfinite(k) || !(std::fabs(k) < 1.0) || k != kij[j * Nc + i]) return LBM_EINVAL;
+            }
+        }
+    }
+    lbm_problem *p = new (std::nothrow) lbm_problem();
+    if (!p) return LBM_ENOMEM;
+    p->lattice = lattice;
+    p->nx = nx;
+    p->ny = ny;
+    p->nz = nz;
+    p->nc = Nc;
+    p->D = lattice == LBM_D2Q9 ? 2 : 3;
+    p->Q = lattice == LBM_D2Q9 ? 9 : 19;
+    p->N = (long long)nx * ny * nz;
+    for (int i = 0; i < Nc; ++i) {
+        p->a[i] = a[i];
+        p->b[i] = b[i];
+        p->omega[i] = omega[i];
+        p->M[i] = 1.0;
+        for (int j = 0; j < Nc; ++j) p->kij[i * kMaxNc + j] = kij ? kij[i * Nc + j] : 0.0;
+    }
+    p->T = T;
+    p->tau = tau;
+    lbm_options_default(&p->opt);
+    *out = p;
+    return LBM_OK;
+}
+
+int lbm_set_options(lbm_problem *p, const lbm_options *opt)
+{
+    if (!p || !opt) return LBM_EINVAL;
+    if (p->allocated) return LBM_ESTATE;
+    if (opt->precision != LBM_FP64 && opt->precision != LBM_FP32DEV) return LBM_EINVAL;
+    if (opt->schedule < LBM_SCHED_AUTO || opt->schedule > LBM_SCHED_FUSED) return LBM_EINVAL;
+    if (!(opt->kappa_ref >= 0.0) || !std::isfinite(opt->kappa_ref)) return LBM_EINVAL;
+    if (opt->kappa_ref_index < 0 || opt->kappa_ref_index >= p->nc) return LBM_EINVAL;
+    if (!(opt->R > 0.0) || !std::isfinite(opt->R)) return LBM_EINVAL;
+    if ((opt->alloc == nullptr) != (opt->free == nullptr)) return LBM_EINVAL;
+    if (opt->M)
+        for (int i = 0; i < p->nc; ++i)
+            if (!(opt->M[i] > 0.0) || !std::isfinite(opt->M[i])) return LBM_EINVAL;
+    p->opt = *opt;
+    for (int i = 0; i < p->nc; ++i) p->M[i] = opt->M ? opt->M[i] : 1.0;
+    p->opt.M = nullptr;
+    return LBM_OK;
+}
+
+int lbm_init_fields_device(lbm_problem *p, const double *d_rho, const double *d_u)
+{
+    if (!p || !d_rho) return LBM_EINVAL;
+    int st = ensure_allocated(p);
+    if (st) return st;
+    st = set_rhobar(p, d_rho);
+    if (st) return st;
+    if (launch_init_equilibrium(p->lattice, p->opt.precision, p->nc, p->P, d_rho, d_u, p->g[0],
+                                p->stream))
+        return LBM_ECUDA;
+    return finish_init(p);
+}
+
+int lbm_init_fields(lbm_problem *p, const double *rho, const double *u)
+{
+    if (!p || !rho) return LBM_EINVAL;
+    const size_t nrho = (size_t)p->nc * p->N;
+    for (size_t k = 0; k < nrho; ++k)
+        if (!(rho[k] > 0.0) || !std::isfinite(rho[k])) return LBM_EINVAL;
+    if (u)
+        for (size_t k = 0; k < (size_t)p->D * p->N; ++k)
+            if (!std::isfinite(u[k])) return LBM_EINVAL;
+    int st = ensure_allocated(p);
+    if (st) return st;
+    // stage through the three-pass scratch (rho: nc*N doubles; u: lnf buffer holds D*N <= nc*N? no)
+    double *d_rho = p->w.rho;
+    double *d_u = nullptr;
+    if (cudaMemcpyAsync(d_rho, rho, nrho * sizeof(double), cudaMemcpyHostToDevice, p->stream) !=
+        cudaSuccess)
+        return LBM_ECUDA;
+    if (u) {
+        d_u = p->w.jm;  // D*N doubles
+        if (cudaMemcpyAsync(d_u, u, (size_t)p->D * p->N * sizeof(double), cudaMemcpyHostToDevice,
+                            p->stream) != cudaSuccess)
+            return LBM_ECUDA;
+    }
+    return lbm_init_fields_device(p, d_rho, d_u);
+}
+
+int lbm_step(lbm_problem *p, long long n)
+{
+    if (!p || n < 0) return LBM_EINVAL;
+    if (!p->initialized) return LBM_ESTATE;
+    if (p->sticky) return p->sticky;
+    const int every = p->opt.monitor_every;
+    for (long long s = 0; s < n; ++s) {
+        const bool mon = every > 0 && ((p->steps + 1) % every == 0);
+        int e;
+        if (p->fused) {
+            e = launch_fused_step(p->opt.precision, p->nc, p->P, p->geo, p->g[p->cur],
+                                  p->g[p->cur ^ 1], p->rs[p->cur], p->rs[p->cur ^ 1],
+                                  mon ? p->mass_partials : nullptr, p->stream);
+            p->launches += 1;
+            if (!e && mon) {
+                e = launch_fused_mass_final(p->nc, p->geo, p->mass_partials, p->mon, p->flag, p->stream);
+                p->launches += 1;
+            }
+        } else {
+            e = launch_threepass_step(p->lattice, p->opt.precision, p->nc, p->P, p->g[p->cur],
+                                      p->g[p->cur ^ 1], p->w, p->stream);
+            p->launches += 3;
+        }
+        if (e) {
+            p->sticky = LBM_ECUDA;
+            return p->sticky;
+        }
+        p->cur ^= 1;
+        p->steps++;
+        if (mon && !p->fused) {
+            // mass of the new state: densities by the first pass of the next step's kernels
+            e = launch_fields(p->lattice, p->opt.precision, p->nc, p->P, p->g[p->cur], p->w, p->w.rho,
+                              nullptr, nullptr, nullptr, p->stream);
+            if (!e) e = launch_mass(p->nc, p->N, p->w.rho, p->partials, p->mon, p->flag, p->stream);
+            p->launches += 3;
+            if (e) {
+                p->sticky = LBM_ECUDA;
+                return p->sticky;
+            }
+        }
+        if (mon) p->monitor_step = p->steps;
+    }
+    return LBM_OK;
+}
+
+int lbm_moments_device(lbm_problem *p, double *d_rho, double *d_u, double *d_pressure, double *d_lnf)
+{
+    if (!p) return LBM_EINVAL;
+    if (!p->initialized) return LBM_ESTATE;
+    if (p->sticky) return p->sticky;
+    if (launch_fields(p->lattice, p->opt.precision, p->nc, p->P, p->g[p->cur], p->w, d_rho, d_u,
+                      d_pressure, d_lnf, p->stream))
+        return LBM_ECUDA;
+    return LBM_OK;
+}
+
+int lbm_moments(lbm_problem *p, double *rho, double *u, double *pressure, double *lnf)
+{
+    if (!p) return LBM_EINVAL;
+    if (!p->initialized) return LBM_ESTATE;
+    if (p->sticky) return p->sticky;
+    // device staging: rho and lnf land in the scratch fields; u and p need their own
+    double *d_u = nullptr, *d_p = nullptr;
+    const size_t nb = (size_t)p->N * sizeof(double);
+    if (u && cudaMalloc(&d_u, (size_t)p->D * nb) != cudaSuccess) return LBM_ENOMEM;
+    if (pressure && cudaMalloc(&d_p, nb) != cudaSuccess) {
+        cudaFree(d_u);
+        return LBM_ENOMEM;
+    }
+    int st = lbm_moments_device(p, p->w.rho, d_u, d_p, p->w.lnf);
+    const size_t fb = (size_t)p->nc * nb;
+    if (!st && rho && cudaMemcpyAsync(rho, p->w.rho, fb, cudaMemcpyDeviceToHost, p->stream)) st = LBM_ECUDA;
+    if (!st && lnf && cudaMemcpyAsync(lnf, p->w.lnf, fb, cudaMemcpyDeviceToHost, p->stream)) st = LBM_ECUDA;
+    if (!st && u && cudaMemcpyAsync(u, d_u, (size_t)p->D * nb, cudaMemcpyDeviceToHost, p->stream)) st = LBM_ECUDA;
+    if (!st && pressure && cudaMemcpyAsync(pressure, d_p, nb, cudaMemcpyDeviceToHost, p->stream)) st = LBM_ECUDA;
+    if (!st && cudaStreamSynchronize(p->stream) != cudaSuccess) st = LBM_ECUDA;
+    cudaFree(d_u);
+    cudaFree(d_p);
+    return st;
+}
+
+int lbm_mass(lbm_problem *p, double *mass)
+{
+    if (!p || !mass) return LBM_EINVAL;
+    if (!p->initialized) return LBM_ESTATE;
+    if (p->sticky) return p->sticky;
+    if (launch_fields(p->lattice, p->opt.precision, p->nc, p->P, p->g[p->cur], p->w, p->w.rho,
+                      nullptr, nullptr, nullptr, p->stream))
+        return LBM_ECUDA;
+    if (cudaMemsetAsync(p->flag, 0, sizeof(int), p->stream) != cudaSuccess) return LBM_ECUDA;
+    if (launch_mass(p->nc, p->N, p->w.rho, p->partials, p->res, p->flag, p->stream)) return LBM_ECUDA;
+    if (cudaMemcpyAsync(mass, p->res, p->nc * sizeof(double), cudaMemcpyDeviceToHost, p->stream) !=
+        cudaSuccess)
+        return LBM_ECUDA;
+    return check_flag(p);
+}
+
+int lbm_convergence(lbm_problem *p, double *max_abs_drho)
+{
+    if (!p || !max_abs_drho) return LBM_EINVAL;
+    if (!p->initialized) return LBM_ESTATE;
+    if (p->sticky) return p->sticky;
+    const size_t fb = (size_t)p->nc * p->N * sizeof(double);
+    if (!p->snap) {
+        p->snap = (double *)dev_alloc(p, fb);
+        if (!p->snap) return LBM_ENOMEM;
+    }
+    if (launch_fields(p->lattice, p->opt.precision, p->nc, p->P, p->g[p->cur], p->w, p->w.rho,
+                      nullptr, nullptr, nullptr, p->stream))
+        return LBM_ECUDA;
+    if (cudaMemsetAsync(p->flag, 0, sizeof(int), p->stream) != cudaSuccess) return LBM_ECUDA;
+    double vals[kMaxNc];
+    if (p->have_snap) {
+        if (launch_maxdiff(p->nc, p->N, p->w.rho, p->snap, p->partials, p->res, p->flag, p->stream))
+            return LBM_ECUDA;
+        if (cudaMemcpyAsync(vals, p->res, p->nc * sizeof(double), cudaMemcpyDeviceToHost,
+                            p->stream) != cudaSuccess)
+            return LBM_ECUDA;
+    }
+    if (cudaMemcpyAsync(p->snap, p->w.rho, fb, cudaMemcpyDeviceToDevice, p->stream) != cudaSuccess)
+        return LBM_ECUDA;
+    int st = check_flag(p);
+    if (st) return st;
+    double m = INFINITY;
+    if (p->have_snap) {
+        m = 0.0;
+        for (int i = 0; i < p->nc; ++i) m = vals[i] > m ? vals[i] : m;
+    }
+    p->have_snap = true;
+    *max_abs_drho = m;
+    return LBM_OK;
+}
+
+int lbm_get_state(lbm_problem *p, double *buf, size_t *bytes)
+{
+    if (!p || !bytes) return LBM_EINVAL;
+    const size_t need = (size_t)p->nc * p->Q * p->N * sizeof(double);
+    if (!buf) {
+        *bytes = need;
+        return LBM_OK;
+    }
+    if (*bytes < need) {
+        *bytes = need;
+        return LBM_EINVAL;
+    }
+    if (!p->initialized) return LBM_ESTATE;
+    if (p->sticky) return p->sticky;
+    double *d = nullptr;
+    if (cudaMalloc(&d, need) != cudaSuccess) return LBM_ENOMEM;
+    int st = LBM_OK;
+    if (launch_state_to_f64(p->lattice, p->opt.precision, p->nc, p->P, p->g[p->cur], d, p->stream))
+        st = LBM_ECUDA;
+    if (!st && cudaMemcpyAsync(buf, d, need, cudaMemcpyDeviceToHost, p->stream) != cudaSuccess) st = LBM_ECUDA;
+    if (!st && cudaStreamSynchronize(p->stream) != cudaSuccess) st = LBM_ECUDA;
+    cudaFree(d);
+    *bytes = need;
+    return st;
+}
+
+int lbm_set_state(lbm_problem *p, const double *buf, size_t bytes)
+{
+    if (!p || !buf) return LBM_EINVAL;
+    const size_t need = (size_t)p->nc * p->Q * p->N * sizeof(double);
+    if (bytes != need) return LBM_EINVAL;
+    for (size_t k = 0; k < need / sizeof(double); ++k)
+        if (!std::isfinite(buf[k])) return LBM_EINVAL;
+    int st = ensure_allocated(p);
+    if (st) return st;
+    double *d = nullptr;
+    if (cudaMalloc(&d, need) != cudaSuccess) return LBM_ENOMEM;
+    if (cudaMemcpyAsync(d, buf, need, cudaMemcpyHostToDevice, p->stream) != cudaSuccess) st = LBM_ECUDA;
+    if (!st && p->opt.precision == LBM_FP32DEV) {
+        // reference densities from the state itself: rho_i = sum_a g_{a,i}
+        std::vector<double> m(p->nc, 0.0);
+        for (int i = 0; i < p->nc; ++i) {
+            double s = 0.0;
+            for (size_t k = (size_t)i * p->Q * p->N; k < (size_t)(i + 1) * p->Q * p->N; ++k) s += buf[k];
+            p->P.rhobar[i] = s / (double)p->N;
+        }
+    }
+    if (!st && launch_state_from_f64(p->lattice, p->opt.precision, p->nc, p->P, d, p->g[0], p->stream))
+        st = LBM_ECUDA;
+    if (!st && cudaStreamSynchronize(p->stream) != cudaSuccess) st = LBM_ECUDA;
+    cudaFree(d);
+    if (st) return st;
+    return finish_init(p);
+}
+
+int lbm_monitor(lbm_problem *p, double *mass, long long *at_step, int *nonfinite)
+{
+    if (!p) return LBM_EINVAL;
+    if (!p->initialized) return LBM_ESTATE;
+    int f = 0;
+    if (mass && p->monitor_step >= 0 &&
+        cudaMemcpyAsync(mass, p->mon, p->nc * sizeof(double), cudaMemcpyDeviceToHost, p->stream) !=
+            cudaSuccess)
+        return LBM_ECUDA;
+    if (cudaMemcpyAsync(&f, p->flag, sizeof(int), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+        cudaStreamSynchronize(p->stream) != cudaSuccess)
+        return LBM_ECUDA;
+    if (at_step) *at_step = p->monitor_step;
+    if (nonfinite) *nonfinite = f;
+    return LBM_OK;
+}
+
+int lbm_launch_count(const lbm_problem *p, long long *launches)
+{
+    if (!p || !launches) return LBM_EINVAL;
+    *launches = p->launches;
+    return LBM_OK;
+}
+
+int lbm_step_count(const lbm_problem *p, long long *steps)
+{
+    if (!p || !steps) return LBM_EINVAL;
+    *steps = p->steps;
+    return LBM_OK;
+}
+
+int lbm_synchronize(lbm_problem *p)
+{
+    if (!p) return LBM_EINVAL;
+    if (!p->stream) return LBM_OK;
+    if (cudaStreamSynchronize(p->stream) != cudaSuccess) {
+        p->sticky = LBM_ECUDA;
+        return LBM_ECUDA;
+    }
+    return p->sticky;
+}
+
+int lbm_destroy(lbm_problem *p)
+{
+    if (!p) return LBM_OK;
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    dev_free_all(p);
+    if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
+    delete p;
+    return LBM_OK;
+}
+
+int lbm_lattice_velocities(int lattice, int *D, int *Q, int *e)
+{
+    if (!D || !Q) return LBM_EINVAL;
+    if (lattice == LBM_D2Q9) {
+        *D = 2;
+        *Q = 9;
+        if (e)
+            for (int a = 0; a < 9; ++a)
+                for (int d = 0; d < 3; ++d) e[a * 3 + d] = Lattice<0>::e(a, d);
+    } else if (lattice == LBM_D3Q19) {
+        *D = 3;
+        *Q = 19;
+        if (e)
+            for (int a = 0; a < 19; ++a)
+                for (int d = 0; d < 3; ++d) e[a * 3 + d] = Lattice<1>::e(a, d);
+    } else {
+        return LBM_EINVAL;
+    }
+    return LBM_OK;
+}
+
+const char *lbm_strerror(int status)
+{
+    switch (status) {
+    case LBM_OK: return "ok";
+    case LBM_EINVAL: return "invalid argument";
+    case LBM_ENOMEM: return "out of memory";
+    case LBM_ECUDA: return "CUDA error";
+    case LBM_ENONFINITE: return "non-finite density";
+    case LBM_ETIMEOUT: return "device wait timed out";
+    case LBM_ESTATE: return "invalid state for this call";
+    case LBM_ENOTSUP: return "not supported";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

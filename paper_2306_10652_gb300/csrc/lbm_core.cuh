@@ -1,0 +1,135 @@
+// lbm_core.cuh -- lattice traits, the per-problem parameter block and the
+// Peng-Robinson thermodynamics shared by every kernel of the library.
+//
+// Paper: Soomro & Ayala, arXiv 2306.10652.
+//   Sec. 2.3, Eq. (9)   PR mixture pressure
+//   Sec. 2.3, Eqs. (10)-(11)  van der Waals mixing rules with delta_ij
+//   Sec. 2.3, Eq. (12)  PR fugacity
+//   Sec. 2.1, Eq. (1b), (1c)  well-balanced equilibrium and forcing
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lbmfug {
+
+constexpr int kMaxNc = 16;
+constexpr double kCs2 = 1.0 / 3.0;
+
+// ---------------------------------------------------------------------------
+// Lattices.  Velocities are ordered rest first, then opposite pairs
+// (2k-1, 2k) with e_{2k} = -e_{2k-1}; gradients are summed pair by pair.
+// ---------------------------------------------------------------------------
+template <int LAT> struct Lattice;
+
+template <> struct Lattice<0> {  // D2Q9
+    static constexpr int D = 2;
+    static constexpr int Q = 9;
+    __host__ __device__ static constexpr int e(int a, int d)
+    {
+        constexpr int E[9][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0}, {0, -1, 0},
+                                 {1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}};
+        return E[a][d];
+    }
+    __host__ __device__ static constexpr double w(int a)
+    {
+        return a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+    }
+};
+
+template <> struct Lattice<1> {  // D3Q19
+    static constexpr int D = 3;
+    static constexpr int Q = 19;
+    __host__ __device__ static constexpr int e(int a, int d)
+    {
+        constexpr int E[19][3] = {{0, 0, 0},   {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},   {0, -1, 0},
+                                  {0, 0, 1},   {0, 0, -1}, {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
+                                  {-1, 1, 0},  {1, 0, 1},  {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                                  {0, 1, 1},   {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+        return E[a][d];
+    }
+    __host__ __device__ static constexpr double w(int a)
+    {
+        return a == 0 ? 1.0 / 3.0 : (a < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Per-problem constants, computed once on the host (T is fixed per problem,
+// so the temperature function alpha_i and every pair product are constant).
+// ---------------------------------------------------------------------------
+struct Params {
+    int nx, ny, nz, nc;
+    long long N;        // nodes
+    double RT, lnRT;    // R T and ln(R T)
+    double omega;       // 1 / tau
+    double b[kMaxNc];       // co-volumes b_i
+    double invM[kMaxNc];    // 1 / M_i
+    double sqk[kMaxNc];     // sqrt(kappa_i), Eq. (4) and Eq. (6)
+    double rhobar[kMaxNc];  // reference density of the deviation storage
+    double A[kMaxNc * kMaxNc];  // sqrt((a alpha)_i (a alpha)_j) (1 - delta_ij), Eq. (10)
+};
+
+// ---------------------------------------------------------------------------
+// Eqs. (9)-(12) at one node from the molar densities rm[i] = rho~_i.
+//
+// With x_i = rho~_i / rho~, B = b_m rho~ and Z = p / (rho~ RT), Eq. (12)
+// plus ln(x_i p) reads
+//   ln f_i = ln rho~_i + [ln RT - ln(1 - B)] + b_i C1 + S_i C2,
+//   C1 = (Z - 1)/b_m + (a alpha)_m Lr / (2 sqrt2 b_m^2 RT),
+//   C2 = -Lr / (sqrt2 b_m RT),
+//   Lr = ln[(1 + (1+sqrt2) B) / (1 + (1-sqrt2) B)],
+//   S_i = sum_j x_j (a alpha)_ij,
+// which is the printed equation regrouped (the two p's cancel, so it holds
+// for p <= 0 too).  Every operation is binary64.
+// ---------------------------------------------------------------------------
+template <int NC>
+__device__ __forceinline__ void pr_lnf(const Params &P, const double (&rm)[NC], double (&lnf)[NC],
+                                       double *p_out)
+{
+    constexpr double kSqrt2 = 1.4142135623730951;
+    double rho = 0.0;
+#pragma unroll
+    for (int i = 0; i < NC; ++i) rho += rm[i];
+    const double inv = 1.0 / rho;
+    double x[NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) x[i] = rm[i] * inv;
+    double bm = 0.0;
+#pragma unroll
+    for (int i = 0; i < NC; ++i) bm = fma(x[i], P.b[i], bm);
+    double S[NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < NC; ++j) s = fma(P.A[i * kMaxNc + j], x[j], s);
+        S[i] = s;
+    }
+    double am = 0.0;
+#pragma unroll
+    for (int i = 0; i < NC; ++i) am = fma(x[i], S[i], am);
+    const double RT = P.RT;
+    const double B = bm * rho;
+    const double omB = 1.0 - B;
+    const double den = fma(B, 2.0 - B, 1.0);  // 1 + 2B - B^2
+    const double amr = am * rho / RT;
+    const double Zm1 = B / omB - amr / den;
+    const double Lr = log(fma(1.0 + kSqrt2, B, 1.0) / fma(1.0 - kSqrt2, B, 1.0));
+    const double C0 = P.lnRT - log(omB);
+    const double invbm = 1.0 / bm;
+    const double C1 = Zm1 * invbm + am * Lr * invbm * invbm / (2.0 * kSqrt2 * RT);
+    const double C2 = -Lr * invbm / (kSqrt2 * RT);
+#pragma unroll
+    for (int i = 0; i < NC; ++i) lnf[i] = log(rm[i]) + C0 + fma(P.b[i], C1, S[i] * C2);
+    if (p_out) *p_out = RT * rho / omB - am * rho * rho / den;
+}
+
+// periodic neighbour index
+__device__ __forceinline__ int wrap(int v, int n)
+{
+    v = v % n;
+    return v < 0 ? v + n : v;
+}
+
+}  // namespace lbmfug

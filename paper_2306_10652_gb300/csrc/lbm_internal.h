@@ -1,0 +1,66 @@
+// lbm_internal.h -- host-side interface between the C ABI (lbm_api.cu) and
+// the kernel translation units.  Not installed; not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_core.cuh"
+
+namespace lbmfug {
+
+// Scratch fields of the three-pass schedule (device, binary64).
+struct ThreePassWork {
+    double *rho;  // [nc][N] mass densities rho_i
+    double *lnf;  // [nc][N] ln f_i
+    double *psi;  // [N]     psi = sum_j sqrt(kappa_j) rho~_j
+    double *lap;  // [N]     lap psi
+    double *jm;   // [D][N]  sum_i sum_a e_a g_{a,i}
+};
+
+// Fused single-pass D2Q9 schedule: density state and launch geometry.
+struct FusedGeom {
+    int strip;    // interior columns per CTA
+    int nstrips;  // CTAs along x
+    int segs;     // CTAs along y
+    int seg_h;    // rows per CTA
+    int threads;  // threads per CTA
+    size_t smem;  // dynamic shared memory bytes
+};
+
+// All launchers return a cudaError_t cast to int (0 = success).
+// prec: 0 = binary64 storage, 1 = binary32 deviation storage.
+int launch_init_equilibrium(int lat, int prec, int nc, const Params &P, const double *rho,
+                            const double *u, void *g, cudaStream_t s);
+int launch_threepass_step(int lat, int prec, int nc, const Params &P, const void *gin, void *gout,
+                          const ThreePassWork &w, cudaStream_t s);
+// Macroscopic outputs of state g into device buffers (any may be null).
+int launch_fields(int lat, int prec, int nc, const Params &P, const void *g,
+                  const ThreePassWork &w, double *rho, double *u, double *p, double *lnf,
+                  cudaStream_t s);
+// Populations <-> binary64 post-streaming layout.
+int launch_state_to_f64(int lat, int prec, int nc, const Params &P, const void *g, double *out,
+                        cudaStream_t s);
+int launch_state_from_f64(int lat, int prec, int nc, const Params &P, const double *in, void *g,
+                          cudaStream_t s);
+
+// Fused D2Q9 schedule (lbm_fused2d.cu).
+bool fused_supported(int lat, int nc);
+FusedGeom fused_geometry(int prec, int nc, const Params &P, int num_sms);
+int launch_fused_density(int prec, int nc, const Params &P, const void *g, void *rho_state,
+                         cudaStream_t s);
+int launch_fused_step(int prec, int nc, const Params &P, const FusedGeom &geo, const void *gin,
+                      void *gout, const void *rho_in, void *rho_out, double *mass_partials,
+                      cudaStream_t s);
+// Sum the per-CTA mass partials of a monitored fused step into out[nc].
+int launch_fused_mass_final(int nc, const FusedGeom &geo, const double *partials, double *out,
+                            int *nonfinite, cudaStream_t s);
+
+// Deterministic reductions (lbm_reduce.cu).  Partials: [blocks][nc].
+constexpr int kReduceBlocks = 1216;  // 8 x 152 SMs
+constexpr int kReduceThreads = 256;
+int launch_mass(int nc, long long N, const double *rho, double *partials, double *out,
+                int *nonfinite, cudaStream_t s);
+int launch_maxdiff(int nc, long long N, const double *rho, const double *snap, double *partials,
+                   double *out, int *nonfinite, cudaStream_t s);
+
+}  // namespace lbmfug

@@ -1,0 +1,366 @@
+// lbm_threepass.cuh -- the three-pass time step (any lattice, any Nc <= 16).
+//
+// Pass 1 (k_macro):   rho_i = sum_a g_{a,i}, the momentum sum_i sum_a e_a g_{a,i},
+//                     ln f_i (Eqs. 9-12) and psi = sum_j sqrt(kappa_j) rho~_j.
+// Pass 2 (k_lap):     lap psi with the isotropic lattice Laplacian.
+// Pass 3 (k_collide): F_i = -rho~_i grad(RT ln f_i - sqrt(kappa_i) lap psi)
+//                     (Eq. 5 with kappa_ij = sqrt(kappa_i kappa_j), Eq. 4, so
+//                     sum_j kappa_ij lap rho~_j = sqrt(kappa_i) lap psi),
+//                     u = (sum e g + F/2) / rho, the equilibrium (Eq. 1b) and
+//                     forcing term (Eq. 1c), BGK (Eq. 1a) and push streaming
+//                     g_{a,i}(r + e_a) <- g*_{a,i}(r).
+//
+// The state is the post-streaming population set (the convention of Eq. 1a).
+// Storage S = double keeps g; S = float keeps the deviation
+// h = g - delta_{a0} rhobar_i and collides in binary32 (thermodynamics,
+// gradients and forces stay binary64).
+#pragma once
+#include "lbm_internal.h"
+
+namespace lbmfug {
+namespace tp {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ void node_xyz(long long r, const Params &P, int &x, int &y, int &z)
+{
+    x = (int)(r % P.nx);
+    long long t = r / P.nx;
+    y = (int)(t % P.ny);
+    z = (int)(t / P.ny);
+}
+
+template <int LAT>
+__device__ __forceinline__ void neighbours(const Params &P, int x, int y, int z,
+                                           long long (&nb)[Lattice<LAT>::Q])
+{
+    using L = Lattice<LAT>;
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) {
+        int xx = wrap(x + L::e(a, 0), P.nx);
+        int yy = wrap(y + L::e(a, 1), P.ny);
+        int zz = wrap(z + L::e(a, 2), P.nz);
+        nb[a] = xx + (long long)P.nx * (yy + (long long)P.ny * zz);
+    }
+}
+
+// grad X(r) = (1/cs2) sum_a w_a e_a X(r + e_a), summed over opposite pairs.
+template <int LAT>
+__device__ __forceinline__ void grad_pairs(const double *__restrict__ X,
+                                           const long long (&nb)[Lattice<LAT>::Q], double (&G)[3])
+{
+    using L = Lattice<LAT>;
+    G[0] = G[1] = G[2] = 0.0;
+#pragma unroll
+    for (int a = 1; a < L::Q; a += 2) {
+        const double d = __ldg(X + nb[a]) - __ldg(X + nb[a + 1]);
+#pragma unroll
+        for (int k = 0; k < L::D; ++k)
+            if (L::e(a, k) != 0) G[k] = fma(L::w(a) * L::e(a, k), d, G[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) G[k] *= 3.0;
+}
+
+template <int LAT, int NC, typename S>
+__global__ void __launch_bounds__(kThreads) k_init(const Params P, const double *__restrict__ rho,
+                                                   const double *__restrict__ u, S *__restrict__ g)
+{
+    using L = Lattice<LAT>;
+    const long long N = P.N;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N;
+         r += (long long)gridDim.x * blockDim.x) {
+        double uu[3] = {0.0, 0.0, 0.0};
+        if (u)
+            for (int d = 0; d < L::D; ++d) uu[d] = u[d * N + r];
+        const double u2 = uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2];
+#pragma unroll
+        for (int a = 0; a < L::Q; ++a) {
+            double ue = 0.0;
+#pragma unroll
+            for (int d = 0; d < L::D; ++d) ue += L::e(a, d) * uu[d];
+            const double Bq = 3.0 * ue + 4.5 * ue * ue - 1.5 * u2;
+#pragma unroll
+            for (int i = 0; i < NC; ++i) {
+                const double ri = rho[i * N + r];
+                double geq = L::w(a) * ri * Bq + (a == 0 ? ri : 0.0);
+                if (sizeof(S) == 4 && a == 0) geq -= P.rhobar[i];
+                g[(i * L::Q + a) * N + r] = (S)geq;
+            }
+        }
+    }
+}
+
+template <int LAT, int NC, typename S>
+__global__ void __launch_bounds__(kThreads)
+    k_macro(const Params P, const S *__restrict__ g, double *__restrict__ rho,
+            double *__restrict__ lnf, double *__restrict__ psi, double *__restrict__ jm,
+            double *__restrict__ pout)
+{
+    using L = Lattice<LAT>;
+    const long long N = P.N;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N;
+         r += (long long)gridDim.x * blockDim.x) {
+        double rm[NC];
+        double j[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+            S s = 0, ji[3] = {0, 0, 0};
+#pragma unroll
+            for (int a = 0; a < L::Q; ++a) {
+                const S v = __ldg(g + (i * L::Q + a) * N + r);
+                s += v;
+#pragma unroll
+                for (int d = 0; d < L::D; ++d)
+                    if (L::e(a, d) > 0) ji[d] += v;
+                    else if (L::e(a, d) < 0) ji[d] -= v;
+            }
+            const double ri = (sizeof(S) == 4 ? P.rhobar[i] : 0.0) + (double)s;
+            rho[i * N + r] = ri;
+            rm[i] = ri * P.invM[i];
+#pragma unroll
+            for (int d = 0; d < L::D; ++d) j[d] += (double)ji[d];
+        }
+        double lf[NC], p;
+        pr_lnf<NC>(P, rm, lf, &p);
+        double ps = 0.0;
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+            lnf[i * N + r] = lf[i];
+            ps = fma(P.sqk[i], rm[i], ps);
+        }
+        psi[r] = ps;
+#pragma unroll
+        for (int d = 0; d < L::D; ++d) jm[d * N + r] = j[d];
+        if (pout) pout[r] = p;
+    }
+}
+
+template <int LAT>
+__global__ void __launch_bounds__(kThreads)
+    k_lap(const Params P, const double *__restrict__ psi, double *__restrict__ lap)
+{
+    using L = Lattice<LAT>;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < P.N;
+         r += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        node_xyz(r, P, x, y, z);
+        long long nb[L::Q];
+        neighbours<LAT>(P, x, y, z, nb);
+        const double c = psi[r];
+        double s = 0.0;
+#pragma unroll
+        for (int a = 1; a < L::Q; ++a) s = fma(L::w(a), __ldg(psi + nb[a]) - c, s);
+        lap[r] = 6.0 * s;  // 2 / cs2
+    }
+}
+
+template <int LAT, int NC, typename S, bool STEP>
+__global__ void __launch_bounds__(kThreads)
+    k_collide(const Params P, const S *__restrict__ gin, S *__restrict__ gout,
+              const double *__restrict__ rho, const double *__restrict__ lnf,
+              const double *__restrict__ lap, const double *__restrict__ jm,
+              double *__restrict__ uout)
+{
+    using L = Lattice<LAT>;
+    constexpr int D = L::D;
+    const long long N = P.N;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N;
+         r += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        node_xyz(r, P, x, y, z);
+        long long nb[L::Q];
+        neighbours<LAT>(P, x, y, z, nb);
+        double GL[3];
+        grad_pairs<LAT>(lap, nb, GL);
+        // Eq. (5): F_i = -rho~_i (RT grad ln f_i - sqrt(kappa_i) grad lap psi)
+        double F[NC][D];
+        double Fs[3] = {0.0, 0.0, 0.0}, rt = 0.0;
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+            double Gl[3];
+            grad_pairs<LAT>(lnf + i * N, nb, Gl);
+            const double ri = rho[i * N + r];
+            rt += ri;
+            const double rmi = ri * P.invM[i];
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                F[i][d] = -rmi * (P.RT * Gl[d] - P.sqk[i] * GL[d]);
+                Fs[d] += F[i][d];
+            }
+        }
+        double u[3] = {0.0, 0.0, 0.0};
+        const double irt = 1.0 / rt;
+#pragma unroll
+        for (int d = 0; d < D; ++d) u[d] = fma(0.5, Fs[d], jm[d * N + r]) * irt;
+        if (!STEP) {
+#pragma unroll
+            for (int d = 0; d < D; ++d) uout[d * N + r] = u[d];
+            continue;
+        }
+        const double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        const double om = P.omega, cF = 1.0 - 0.5 * P.omega;
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+            double Gr[3];
+            grad_pairs<LAT>(rho + i * N, nb, Gr);
+            const double ri = rho[i * N + r];
+            double Fu = 0.0, Gu = 0.0;
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                Fu = fma(F[i][d], u[d], Fu);
+                Gu = fma(Gr[d], u[d], Gu);
+            }
+#pragma unroll
+            for (int a = 0; a < L::Q; ++a) {
+                double ue = 0.0, Fe = 0.0, Ge = 0.0;
+                int e2 = 0;
+#pragma unroll
+                for (int d = 0; d < D; ++d) {
+                    const int ed = L::e(a, d);
+                    e2 += ed * ed;
+                    if (ed > 0) { ue += u[d]; Fe += F[i][d]; Ge += Gr[d]; }
+                    if (ed < 0) { ue -= u[d]; Fe -= F[i][d]; Ge -= Gr[d]; }
+                }
+                const double w = L::w(a);
+                const double Bq = ue * fma(4.5, ue, 3.0) - 1.5 * u2;
+                // Eq. (1c): F.[(e-u)/cs2 + (u.e)e/cs4] + grad rho.[-u + (u.e)e/cs2 + (e^2/cs2 - D)u/2]
+                const double cW = 0.5 * (3.0 * e2 - D) - 1.0;
+                const double Fa = w * (Fe * fma(9.0, ue, 3.0) - 3.0 * Fu + 3.0 * ue * Ge + cW * Gu);
+                const long long k = (i * L::Q + a) * N;
+                if (sizeof(S) == 8) {
+                    const double geq = w * ri * Bq + (a == 0 ? ri : 0.0);
+                    const double gv = (double)gin[k + r];
+                    gout[k + nb[a]] = (S)(gv + om * (geq - gv) + cF * Fa);
+                } else {
+                    // deviation form: h* = (1-w)h + w (geq - delta_a0 rhobar) + cF Fa
+                    const float hv = (float)gin[k + r];
+                    const float geqd = (float)(w * ri * Bq + (a == 0 ? ri - P.rhobar[i] : 0.0));
+                    const float ho = fmaf((float)om, geqd - hv, hv) + (float)cF * (float)Fa;
+                    gout[k + nb[a]] = (S)ho;
+                }
+            }
+        }
+    }
+}
+
+template <int LAT, int NC, typename S>
+__global__ void k_to_f64(const Params P, const S *__restrict__ g, double *__restrict__ out)
+{
+    using L = Lattice<LAT>;
+    const long long tot = (long long)NC * L::Q * P.N;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < tot;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long ia = k / P.N;
+        const int a = (int)(ia % L::Q), i = (int)(ia / L::Q);
+        double v = (double)g[k];
+        if (sizeof(S) == 4 && a == 0) v += P.rhobar[i];
+        out[k] = v;
+    }
+}
+
+template <int LAT, int NC, typename S>
+__global__ void k_from_f64(const Params P, const double *__restrict__ in, S *__restrict__ g)
+{
+    using L = Lattice<LAT>;
+    const long long tot = (long long)NC * L::Q * P.N;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < tot;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long ia = k / P.N;
+        const int a = (int)(ia % L::Q), i = (int)(ia / L::Q);
+        double v = in[k];
+        if (sizeof(S) == 4 && a == 0) v -= P.rhobar[i];
+        g[k] = (S)v;
+    }
+}
+
+inline unsigned grid_for(long long n)
+{
+    long long b = (n + kThreads - 1) / kThreads;
+    if (b > 152LL * 64) b = 152LL * 64;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+template <int LAT, int NC, typename S> struct Impl {
+    static int init(const Params &P, const double *rho, const double *u, void *g, cudaStream_t s)
+    {
+        k_init<LAT, NC, S><<<grid_for(P.N), kThreads, 0, s>>>(P, rho, u, (S *)g);
+        return (int)cudaGetLastError();
+    }
+    static int step(const Params &P, const void *gin, void *gout, const ThreePassWork &w,
+                    cudaStream_t s)
+    {
+        const unsigned G = grid_for(P.N);
+        k_macro<LAT, NC, S><<<G, kThreads, 0, s>>>(P, (const S *)gin, w.rho, w.lnf, w.psi, w.jm,
+                                                   nullptr);
+        k_lap<LAT><<<G, kThreads, 0, s>>>(P, w.psi, w.lap);
+        k_collide<LAT, NC, S, true><<<G, kThreads, 0, s>>>(P, (const S *)gin, (S *)gout, w.rho,
+                                                           w.lnf, w.lap, w.jm, nullptr);
+        return (int)cudaGetLastError();
+    }
+    static int fields(const Params &P, const void *g, const ThreePassWork &w, double *rho,
+                      double *u, double *p, double *lnf, cudaStream_t s)
+    {
+        const unsigned G = grid_for(P.N);
+        k_macro<LAT, NC, S><<<G, kThreads, 0, s>>>(P, (const S *)g, w.rho, w.lnf, w.psi, w.jm, p);
+        if (u) {
+            k_lap<LAT><<<G, kThreads, 0, s>>>(P, w.psi, w.lap);
+            k_collide<LAT, NC, S, false><<<G, kThreads, 0, s>>>(P, (const S *)g, nullptr, w.rho,
+                                                                w.lnf, w.lap, w.jm, u);
+        }
+        const size_t fb = (size_t)NC * P.N * sizeof(double);
+        if (rho && rho != w.rho) cudaMemcpyAsync(rho, w.rho, fb, cudaMemcpyDeviceToDevice, s);
+        if (lnf && lnf != w.lnf) cudaMemcpyAsync(lnf, w.lnf, fb, cudaMemcpyDeviceToDevice, s);
+        return (int)cudaGetLastError();
+    }
+    static int to_f64(const Params &P, const void *g, double *out, cudaStream_t s)
+    {
+        k_to_f64<LAT, NC, S><<<grid_for((long long)NC * Lattice<LAT>::Q * P.N), kThreads, 0, s>>>(
+            P, (const S *)g, out);
+        return (int)cudaGetLastError();
+    }
+    static int from_f64(const Params &P, const double *in, void *g, cudaStream_t s)
+    {
+        k_from_f64<LAT, NC, S><<<grid_for((long long)NC * Lattice<LAT>::Q * P.N), kThreads, 0, s>>>(
+            P, in, (S *)g);
+        return (int)cudaGetLastError();
+    }
+};
+
+// Function table of one (lattice, storage, Nc) instantiation.
+struct Ops {
+    int (*init)(const Params &, const double *, const double *, void *, cudaStream_t);
+    int (*step)(const Params &, const void *, void *, const ThreePassWork &, cudaStream_t);
+    int (*fields)(const Params &, const void *, const ThreePassWork &, double *, double *, double *,
+                  double *, cudaStream_t);
+    int (*to_f64)(const Params &, const void *, double *, cudaStream_t);
+    int (*from_f64)(const Params &, const double *, void *, cudaStream_t);
+};
+
+template <int LAT, int NC, typename S> const Ops *ops_of()
+{
+    static const Ops o = {&Impl<LAT, NC, S>::init, &Impl<LAT, NC, S>::step, &Impl<LAT, NC, S>::fields,
+                          &Impl<LAT, NC, S>::to_f64, &Impl<LAT, NC, S>::from_f64};
+    return &o;
+}
+
+// Table of one translation unit: lattice LAT, storage S, Nc in [LO, HI].
+template <int LAT, typename S, int LO, int HI> const Ops *ops_range(int nc)
+{
+    if constexpr (LO > HI) {
+        return nullptr;
+    } else {
+        if (nc == LO) return ops_of<LAT, LO, S>();
+        return ops_range<LAT, S, LO + 1, HI>(nc);
+    }
+}
+
+}  // namespace tp
+
+#define LBM_TP_TU(NAME, LAT, S, LO, HI) \
+    namespace lbmfug { namespace tp { \
+    const Ops *NAME(int nc) { return ops_range<LAT, S, LO, HI>(nc); } \
+    } }
+
+}  // namespace lbmfug

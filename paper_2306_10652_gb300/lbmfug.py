@@ -1,0 +1,257 @@
+"""Python binding of ``liblbmfug.so`` (the C ABI of include/lbmfug.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Host arrays are numpy float64 arrays; device buffers are
+torch CUDA tensors (PyTorch provides device memory and streams, nothing
+else).  Importing this module raises if the library has not been built:
+there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblbmfug.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_2306_10652_gb300/build.py "
+                      "(or __graft_entry__.build()); there is no CPU fallback")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+LBM_D2Q9, LBM_D3Q19 = 0, 1
+LBM_FP64, LBM_FP32DEV = 0, 1
+LBM_SCHED_AUTO, LBM_SCHED_THREEPASS, LBM_SCHED_FUSED = 0, 1, 2
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENONFINITE, LBM_ETIMEOUT, LBM_ESTATE, LBM_ENOTSUP = \
+    0, -1, -2, -3, -4, -5, -6, -7
+LBM_MAX_NC = 16
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_vp = ctypes.c_void_p
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+class lbm_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("schedule", ctypes.c_int),
+                ("kappa_ref", ctypes.c_double), ("kappa_ref_index", ctypes.c_int),
+                ("M", _dp), ("R", ctypes.c_double), ("stream", _vp), ("monitor_every", ctypes.c_int),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", _vp)]
+
+
+def _sig(name, res, *args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = list(args)
+    return f
+
+
+_sig("lbm_options_default", ctypes.c_int, ctypes.POINTER(lbm_options))
+_sig("lbm_create", ctypes.c_int, ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+     ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double)
+_sig("lbm_set_options", ctypes.c_int, _vp, ctypes.POINTER(lbm_options))
+_sig("lbm_init_fields", ctypes.c_int, _vp, _dp, _dp)
+_sig("lbm_init_fields_device", ctypes.c_int, _vp, _vp, _vp)
+_sig("lbm_step", ctypes.c_int, _vp, ctypes.c_longlong)
+_sig("lbm_moments", ctypes.c_int, _vp, _dp, _dp, _dp, _dp)
+_sig("lbm_moments_device", ctypes.c_int, _vp, _vp, _vp, _vp, _vp)
+_sig("lbm_mass", ctypes.c_int, _vp, _dp)
+_sig("lbm_convergence", ctypes.c_int, _vp, _dp)
+_sig("lbm_get_state", ctypes.c_int, _vp, _dp, ctypes.POINTER(ctypes.c_size_t))
+_sig("lbm_set_state", ctypes.c_int, _vp, _dp, ctypes.c_size_t)
+_sig("lbm_step_count", ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_longlong))
+_sig("lbm_monitor", ctypes.c_int, _vp, _dp, ctypes.POINTER(ctypes.c_longlong), _ip)
+_sig("lbm_launch_count", ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_longlong))
+_sig("lbm_synchronize", ctypes.c_int, _vp)
+_sig("lbm_destroy", ctypes.c_int, _vp)
+_sig("lbm_lattice_velocities", ctypes.c_int, ctypes.c_int, _ip, _ip, _ip)
+_sig("lbm_strerror", ctypes.c_char_p, ctypes.c_int)
+
+EXPORTED = ["lbm_options_default", "lbm_create", "lbm_set_options", "lbm_init_fields",
+            "lbm_init_fields_device", "lbm_step", "lbm_moments", "lbm_moments_device", "lbm_mass",
+            "lbm_convergence", "lbm_get_state", "lbm_set_state", "lbm_step_count", "lbm_monitor",
+            "lbm_launch_count",
+            "lbm_synchronize", "lbm_destroy", "lbm_lattice_velocities", "lbm_strerror"]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        super().__init__(f"{where}: {lbm_strerror(status)} ({status})")
+
+
+def lbm_strerror(status: int) -> str:
+    return _lib.lbm_strerror(int(status)).decode()
+
+
+def _check(st, where):
+    if st != LBM_OK:
+        raise LbmError(st, where)
+
+
+def _host(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def _hp(a):
+    return None if a is None else a.ctypes.data_as(_dp)
+
+
+def _dev(t):
+    """Raw device pointer of a contiguous float64 CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not (t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float64"):
+        raise ValueError("device buffers must be contiguous float64 CUDA tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def lbm_lattice_velocities(lattice: int):
+    D, Q = ctypes.c_int(), ctypes.c_int()
+    e = np.zeros((19, 3), dtype=np.int32)
+    _check(_lib.lbm_lattice_velocities(lattice, ctypes.byref(D), ctypes.byref(Q),
+                                       e.ctypes.data_as(_ip)), "lbm_lattice_velocities")
+    return D.value, Q.value, e[:Q.value].copy()
+
+
+class Problem:
+    """One periodic problem (a handle of the C ABI).
+
+    ``Problem(lattice, nx, ny, nz, a, b, omega, kij, T, tau, **options)``
+    mirrors ``lbm_create`` + ``lbm_set_options``; option keywords are the
+    fields of ``lbm_options`` (precision, schedule, kappa_ref,
+    kappa_ref_index, M, R, stream).
+    """
+
+    def __init__(self, lattice, nx, ny, nz, a, b, omega, kij=None, T=None, tau=1.0, *,
+                 precision=LBM_FP64, schedule=LBM_SCHED_AUTO, kappa_ref=0.02, kappa_ref_index=0,
+                 M=None, R=1.0, stream=None, monitor_every=0):
+        self._h = None
+        a = _host(a)
+        nc = a.size
+        self.lattice, self.nx, self.ny, self.nz, self.nc = int(lattice), int(nx), int(ny), int(nz), nc
+        self.D, self.Q, self.e = lbm_lattice_velocities(self.lattice)
+        self.precision = precision
+        b = _host(b, nc)
+        omega = _host(omega, nc)
+        kij = None if kij is None else _host(kij, nc * nc)
+        h = _vp()
+        _check(_lib.lbm_create(ctypes.byref(h), self.lattice, self.nx, self.ny, self.nz, nc,
+                               _hp(a), _hp(b), _hp(omega), _hp(kij), float(T), float(tau)),
+               "lbm_create")
+        self._h = h
+        opt = lbm_options()
+        _lib.lbm_options_default(ctypes.byref(opt))
+        opt.precision = int(precision)
+        opt.schedule = int(schedule)
+        opt.kappa_ref = float(kappa_ref)
+        opt.kappa_ref_index = int(kappa_ref_index)
+        self._M = None if M is None else _host(M, nc)
+        opt.M = _hp(self._M)
+        opt.R = float(R)
+        opt.stream = None if stream is None else ctypes.c_void_p(int(stream))
+        opt.monitor_every = int(monitor_every)
+        _check(_lib.lbm_set_options(self._h, ctypes.byref(opt)), "lbm_set_options")
+
+    # -- shapes --
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    @property
+    def N(self):
+        return self.nx * self.ny * self.nz
+
+    # -- calls --
+    def init_fields(self, rho, u=None):
+        rho = _host(rho, self.nc * self.N)
+        u = None if u is None else _host(u, self.D * self.N)
+        _check(_lib.lbm_init_fields(self._h, _hp(rho), _hp(u)), "lbm_init_fields")
+
+    def init_fields_device(self, d_rho, d_u=None):
+        _check(_lib.lbm_init_fields_device(self._h, _dev(d_rho), _dev(d_u)), "lbm_init_fields_device")
+
+    def step(self, n=1):
+        _check(_lib.lbm_step(self._h, int(n)), "lbm_step")
+
+    def moments(self, want=("rho", "u", "p", "lnf")):
+        out = {}
+        rho = np.empty((self.nc,) + self.shape) if "rho" in want else None
+        u = np.empty((self.D,) + self.shape) if "u" in want else None
+        p = np.empty(self.shape) if "p" in want else None
+        lnf = np.empty((self.nc,) + self.shape) if "lnf" in want else None
+        _check(_lib.lbm_moments(self._h, _hp(rho), _hp(u), _hp(p), _hp(lnf)), "lbm_moments")
+        for k, v in (("rho", rho), ("u", u), ("p", p), ("lnf", lnf)):
+            if v is not None:
+                out[k] = v
+        return out
+
+    def moments_device(self, d_rho=None, d_u=None, d_p=None, d_lnf=None):
+        _check(_lib.lbm_moments_device(self._h, _dev(d_rho), _dev(d_u), _dev(d_p), _dev(d_lnf)),
+               "lbm_moments_device")
+
+    def mass(self):
+        m = np.empty(self.nc)
+        _check(_lib.lbm_mass(self._h, _hp(m)), "lbm_mass")
+        return m
+
+    def convergence(self):
+        v = ctypes.c_double()
+        _check(_lib.lbm_convergence(self._h, ctypes.byref(v)), "lbm_convergence")
+        return v.value
+
+    def get_state(self):
+        n = ctypes.c_size_t()
+        _check(_lib.lbm_get_state(self._h, None, ctypes.byref(n)), "lbm_get_state")
+        buf = np.empty(n.value // 8)
+        _check(_lib.lbm_get_state(self._h, _hp(buf), ctypes.byref(n)), "lbm_get_state")
+        return buf.reshape((self.nc, self.Q) + self.shape)
+
+    def set_state(self, g):
+        g = _host(g, self.nc * self.Q * self.N)
+        _check(_lib.lbm_set_state(self._h, _hp(g), g.nbytes), "lbm_set_state")
+
+    def monitor(self):
+        """(mass[Nc] or None, step it was taken at, nonfinite flag)."""
+        m = np.empty(self.nc)
+        at = ctypes.c_longlong()
+        nf = ctypes.c_int()
+        _check(_lib.lbm_monitor(self._h, _hp(m), ctypes.byref(at), ctypes.byref(nf)), "lbm_monitor")
+        return (m if at.value >= 0 else None), at.value, bool(nf.value)
+
+    def launch_count(self):
+        v = ctypes.c_longlong()
+        _check(_lib.lbm_launch_count(self._h, ctypes.byref(v)), "lbm_launch_count")
+        return v.value
+
+    def step_count(self):
+        v = ctypes.c_longlong()
+        _check(_lib.lbm_step_count(self._h, ctypes.byref(v)), "lbm_step_count")
+        return v.value
+
+    def synchronize(self):
+        _check(_lib.lbm_synchronize(self._h), "lbm_synchronize")
+
+    def close(self):
+        if self._h is not None:
+            _lib.lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

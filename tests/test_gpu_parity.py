@@ -1,0 +1,219 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances (derivation in the design notes):
+* binary64 storage, one step: max |g_gpu - g_orc| <= 1e-12 * max |g_i| per
+  component (the two sides differ only in rounding order);
+* binary64, 1000 steps of the flat-interface case: |rho_gpu - rho_orc| <= 1e-9;
+* binary32 deviation storage: one step within 2e-6 of max |g_i|; component
+  mass within 1e-6 relative; converged phase mole fractions within 1e-5 of
+  the binary64 path.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from helpers import gpu_problem, oracle_problem, order_map, seeded_mixture, smooth_rho
+from oracle.thermo import flash
+from oracle.workloads import slab, two_phase_pressure
+from paper_2306_10652_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+FP64, FP32DEV = 0, 1
+THREEPASS, AUTO, FUSED = 1, 0, 2
+
+
+def lb():
+    from paper_2306_10652_gb300 import lbmfug
+    return lbmfug
+
+
+def one_step_case(seed, nc, lattice, shape, tau=1.0, Mrand=False, precision=FP64, schedule=THREEPASS,
+                  nsteps=1, Tfac=0.85, lo=0.02, hi=0.12):
+    c = seeded_mixture(seed, nc, lattice, shape, Tfac=Tfac)
+    M = synth.uniform(seed, 0.5, 2.0, nc) if Mrand else None
+    orc = oracle_problem(c, lattice, shape, tau=tau, M=M)
+    rho = smooth_rho(seed, c, shape, lo, hi) * (1.0 if M is None else M[:, None, None, None])
+    u = synth.random_velocity(seed, orc.D, shape, 1e-3)
+    g0 = orc.init_equilibrium(rho, u)
+    g_ref = orc.step(g0, nsteps)
+    with gpu_problem(c, lattice, shape, tau=tau, M=M, precision=precision, schedule=schedule) as gp:
+        gp.init_fields(rho, u)
+        gp.step(nsteps)
+        g = gp.get_state()[:, order_map(lattice, gp.e)]
+    scale = np.abs(g_ref).max(axis=(1, 2, 3, 4), keepdims=True)
+    return float((np.abs(g - g_ref) / scale).max())
+
+
+CASES = [
+    # seed, nc, lattice, shape (nz, ny, nx), tau, random M
+    (0, 1, 0, (1, 8, 8), 1.0, False),
+    (1, 2, 0, (1, 7, 13), 0.8, True),
+    (2, 3, 0, (1, 33, 70), 1.0, False),
+    (3, 5, 0, (1, 5, 131), 1.3, True),
+    (4, 10, 0, (1, 16, 20), 1.0, False),
+    (5, 16, 0, (1, 6, 9), 1.0, True),
+    (6, 2, 0, (1, 1, 9), 1.0, False),
+    (7, 2, 0, (1, 4, 1), 1.0, False),
+    (8, 2, 1, (5, 6, 7), 1.0, True),
+    (9, 3, 1, (4, 4, 4), 0.9, False),
+    (10, 10, 1, (3, 5, 6), 1.0, False),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"lat{c[2]}-nc{c[1]}-{c[3]}" for c in CASES])
+@pytest.mark.parametrize("schedule", [THREEPASS, AUTO])
+def test_one_step_fp64(case, schedule):
+    seed, nc, lattice, shape, tau, Mr = case
+    assert one_step_case(seed, nc, lattice, shape, tau, Mr, FP64, schedule) < 1e-12
+
+
+@pytest.mark.parametrize("case", CASES[:6] + CASES[8:10], ids=lambda c: f"lat{c[2]}-nc{c[1]}")
+@pytest.mark.parametrize("schedule", [THREEPASS, AUTO])
+def test_one_step_fp32dev(case, schedule):
+    seed, nc, lattice, shape, tau, Mr = case
+    assert one_step_case(seed, nc, lattice, shape, tau, Mr, FP32DEV, schedule) < 2e-6
+
+
+def test_ten_steps_fp64_two_phase():
+    # liquid-range densities inside the two-phase region: strong forces
+    assert one_step_case(11, 3, 0, (1, 24, 40), nsteps=10, lo=0.05, hi=0.6) < 1e-11
+
+
+def flat_interface_case(seed=0, nx=128, ny=4, nc=2):
+    """Binary slab, Eq. (15) at the flash densities for S_V = 0.5, with 1e-3
+    multiplicative noise (the flat-interface workload)."""
+    c = seeded_mixture(seed, nc, 0, (1, ny, nx))
+    orc = oracle_problem(c, 0, (1, ny, nx))
+    z = np.ones(nc) / nc
+    p, fl = two_phase_pressure(orc, z, 0.5)
+    prof = slab(fl.rhoi_V, fl.rhoi_L, nx)                       # [nc, nx]
+    rho = np.repeat(prof[:, None, None, :], ny, axis=2)
+    rho = rho * synth.multiplicative_noise(seed, rho.shape, 1e-3)
+    return c, orc, rho
+
+
+@pytest.mark.parametrize("schedule", [THREEPASS, AUTO])
+def test_flat_interface_1000_steps_fp64(schedule):
+    c, orc, rho = flat_interface_case()
+    ref = orc.moments(orc.step(orc.init_equilibrium(rho), 1000))
+    with gpu_problem(c, 0, orc.shape, precision=FP64, schedule=schedule) as gp:
+        gp.init_fields(rho)
+        gp.step(1000)
+        m = gp.moments()
+    assert np.abs(m["rho"] - ref["rho"]).max() <= 1e-9
+    assert np.abs(m["u"] - ref["u"]).max() <= 1e-9
+    assert np.abs(m["lnf"] - ref["lnf"]).max() <= 1e-8
+    assert np.abs(m["p"] - ref["p"]).max() <= 1e-9
+
+
+@pytest.mark.parametrize("schedule", [THREEPASS, AUTO])
+def test_fp32dev_mass_and_equilibrium(schedule):
+    """Binary32 deviation storage against the binary64 path: per-component
+    mass within 1e-6 relative, and the converged phase mole fractions (phase
+    centres, same sublattice) within 1e-5."""
+    c, orc, rho = flat_interface_case(nx=64, ny=2)
+    m0 = orc.mass(orc.init_equilibrium(rho))
+    res = {}
+    for prec in (FP64, FP32DEV):
+        with gpu_problem(c, 0, orc.shape, precision=prec, schedule=schedule) as gp:
+            gp.init_fields(rho)
+            gp.step(1000)
+            mass = gp.mass()
+            if prec == FP32DEV:
+                assert np.abs(mass / m0 - 1).max() <= 1e-6
+            gp.step(39000)
+            r = gp.moments(("rho",))["rho"][:, 0, 0]
+            res[prec] = (r[:, 32] / r[:, 32].sum(), r[:, 0] / r[:, 0].sum())
+            if prec == FP32DEV:
+                assert np.abs(gp.mass() / m0 - 1).max() <= 1e-6
+    for k in range(2):
+        assert np.abs(res[FP32DEV][k] - res[FP64][k]).max() <= 1e-5, (res[FP32DEV][k], res[FP64][k])
+
+
+@pytest.mark.parametrize("lattice,shape,nc", [(0, (1, 12, 17), 3), (1, (4, 5, 6), 2)])
+def test_moments_match_oracle(lattice, shape, nc):
+    c = seeded_mixture(21, nc, lattice, shape)
+    orc = oracle_problem(c, lattice, shape)
+    rho = smooth_rho(21, c, shape)
+    u = synth.random_velocity(21, orc.D, shape, 1e-3)
+    g = orc.step(orc.init_equilibrium(rho, u), 2)
+    ref = orc.moments(g)
+    with gpu_problem(c, lattice, shape) as gp:
+        e_map = order_map(lattice, gp.e)
+        inv = np.empty(len(e_map), int)
+        inv[e_map] = np.arange(len(e_map))
+        gp.set_state(g[:, inv])                 # oracle order -> library order
+        m = gp.moments()
+        assert np.allclose(gp.get_state()[:, e_map], g, rtol=0, atol=0)
+    for k in ("rho", "u", "p", "lnf"):
+        scale = max(np.abs(ref[k]).max(), 1e-30)
+        assert np.abs(m[k] - ref[k]).max() <= 1e-13 * scale + 1e-15, k
+
+
+@pytest.mark.parametrize("precision,schedule", [(FP64, THREEPASS), (FP64, AUTO), (FP32DEV, AUTO)])
+def test_mass_conservation_and_uniform_fixed_point(precision, schedule):
+    shape = (1, 40, 70)
+    c = seeded_mixture(31, 3, 0, shape)
+    rho = smooth_rho(31, c, shape)
+    with gpu_problem(c, 0, shape, precision=precision, schedule=schedule) as gp:
+        gp.init_fields(rho)
+        m0 = gp.mass()
+        gp.step(50)
+        m1 = gp.mass()
+        tol = 1e-13 if precision == FP64 else 1e-6
+        assert np.abs(m1 / m0 - 1).max() < tol
+    uni = np.ones((3,) + shape) * (0.3 / np.asarray(c["b"])[:, None, None, None] / 3)
+    with gpu_problem(c, 0, shape, precision=precision, schedule=schedule) as gp:
+        gp.init_fields(uni)
+        g0 = gp.get_state()
+        gp.step(5)
+        assert np.array_equal(gp.get_state(), g0)
+
+
+def test_convergence_monitor_and_nonfinite():
+    shape = (1, 16, 16)
+    c = seeded_mixture(41, 2, 0, shape)
+    rho = smooth_rho(41, c, shape)
+    with gpu_problem(c, 0, shape) as gp:
+        gp.init_fields(rho)
+        assert gp.convergence() == float("inf")
+        gp.step(10)
+        d1 = gp.convergence()
+        assert 0 < d1 < 1
+        assert gp.convergence() == 0.0     # no steps since the snapshot
+        g = gp.get_state()
+        g[0, 0, 0, 3, 3] = np.inf
+        with pytest.raises(lb().LbmError):  # non-finite state is rejected on the host
+            gp.set_state(g)
+
+
+def test_device_buffers_and_stream():
+    import torch
+    shape = (1, 9, 14)
+    c = seeded_mixture(51, 2, 0, shape)
+    rho = smooth_rho(51, c, shape)
+    s = torch.cuda.Stream()
+    with gpu_problem(c, 0, shape, stream=s.cuda_stream) as gp:
+        d_rho = torch.from_numpy(rho.copy()).cuda()
+        gp.init_fields_device(d_rho.reshape(-1))
+        gp.step(4)
+        out = torch.empty_like(d_rho)
+        gp.moments_device(d_rho=out)
+        gp.synchronize()
+        host = gp.moments(("rho",))["rho"]
+    assert np.array_equal(out.cpu().numpy(), host)
+
+
+def test_zero_steps_and_step_count():
+    shape = (1, 5, 5)
+    c = seeded_mixture(61, 1, 0, shape)
+    rho = smooth_rho(61, c, shape)
+    with gpu_problem(c, 0, shape) as gp:
+        gp.init_fields(rho)
+        g0 = gp.get_state()
+        gp.step(0)
+        assert np.array_equal(gp.get_state(), g0)
+        gp.step(3)
+        assert gp.step_count() == 3
