@@ -130,7 +130,9 @@ def run_gpu(args):
     d, case = load_case(args.nc)
     nx, ny = d["nx"], d["ny"]
     nc = case["nc"]
-    prec = {"fp64": lbmfug.LBM_FP64, "fp32dev": lbmfug.LBM_FP32DEV}[args.precision]
+    prec = {"fp64": lbmfug.LBM_FP64, "fp32dev": lbmfug.LBM_FP32DEV, "fp32": lbmfug.LBM_FP32}[args.precision]
+    if args.grid:
+        nx, ny = (int(v) for v in args.grid.lower().split("x"))
     sched = {"auto": lbmfug.LBM_SCHED_AUTO, "threepass": lbmfug.LBM_SCHED_THREEPASS,
              "fused": lbmfug.LBM_SCHED_FUSED}[args.schedule]
     rho = initial_density(d, case, nx, ny)
@@ -173,7 +175,8 @@ def run_gpu(args):
     step_ms = ms / args.steps
     pk, pk_kind = peaks()
     achieved = alg_bytes_per_launch / (step_ms * 1e-3) / 1e9  # GB/s, whole step per launch
-    e2e = run_e2e(args, lbmfug, case, rho, nx, ny, prec, sched, local) if rank == 0 else None
+    e2e = run_e2e(args, lbmfug, case, rho, nx, ny, prec, sched, local) \
+        if (rank == 0 and not args.no_e2e) else None
     if rank != 0:
         if ws > 1:
             dist.destroy_process_group()
@@ -183,7 +186,7 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if prec == lbmfug.LBM_FP32DEV else "f64",
+        "vs_baseline": None, "dtype": "f64" if prec == lbmfug.LBM_FP64 else "f32",
         "data": "synthetic (seeded PR mixture, uniform state in the spinodal region + 1% noise)",
         "config": {"workload": f"spinodal decomposition D2Q9 {nx}x{ny} periodic, Nc={nc}",
                    "lattice": "D2Q9", "nx": nx, "ny": ny, "nc": nc,
@@ -289,7 +292,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--nc", type=int, default=10)
-    ap.add_argument("--precision", default="fp32dev", choices=["fp32dev", "fp64"])
+    ap.add_argument("--precision", default="fp32dev", choices=["fp32dev", "fp32", "fp64"])
+    ap.add_argument("--grid", default=None, help="NXxNY override of the workload grid (profiling)")
+    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--schedule", default="auto", choices=["auto", "threepass", "fused"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -43,11 +43,21 @@ extern "C" {
 
 enum lbm_lattice { LBM_D2Q9 = 0, LBM_D3Q19 = 1 };
 
-/* Population storage.  LBM_FP64 stores g in binary64 and computes every step
- * in binary64 (the plain path).  LBM_FP32DEV stores g_{a,i} - delta_{a0} rhobar_i
- * (deviation from the rest equilibrium of the mean density) in binary32, with
- * the collision in binary32 and the thermodynamics in binary64. */
-enum lbm_precision { LBM_FP64 = 0, LBM_FP32DEV = 1 };
+/* Population storage and arithmetic.
+ *  LBM_FP64:    all Q populations stored in binary64, every operation binary64
+ *               (the plain path).
+ *  LBM_FP32DEV: populations stored as their deviation from the rest
+ *               equilibrium (rho_i, 0, ..., 0) of Eq. (1b): the Q-1 moving
+ *               populations in binary32, with the density rho_i itself kept
+ *               exactly as a binary32 pair (hi + lo) that each step moves by
+ *               compensated sums of the populations that left and arrived
+ *               (component mass conserved to the rounding of the pair);
+ *               collision in binary32; Peng-Robinson mixture, fugacities,
+ *               forces and mass sums in binary64.
+ *  LBM_FP32:    the LBM_FP32DEV storage, with the thermodynamics and forces of
+ *               the fused schedule in binary32 too (the three-pass schedule
+ *               keeps them in binary64). */
+enum lbm_precision { LBM_FP64 = 0, LBM_FP32DEV = 1, LBM_FP32 = 2 };
 
 /* Kernel schedule: LBM_SCHED_AUTO picks the fused single-pass kernel where it
  * exists (D2Q9) and the three-pass kernels otherwise. */

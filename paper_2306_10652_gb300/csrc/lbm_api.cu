@@ -31,8 +31,7 @@ struct lbm_problem {
     int sticky = LBM_OK;
     bool fused = false;
     FusedGeom geo{};
-    void *g[2] = {nullptr, nullptr};
-    void *rs[2] = {nullptr, nullptr};  // fused schedule: density state
+    StateBufs st[2];  // two time levels
     int cur = 0;
     ThreePassWork w{};
     double *snap = nullptr;
@@ -52,7 +51,10 @@ namespace {
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ECUDA; }
 
-int pstore_bytes(const lbm_problem *p) { return p->opt.precision == LBM_FP32DEV ? 4 : 8; }
+int pstore_bytes(const lbm_problem *p) { return p->opt.precision == LBM_FP64 ? 8 : 4; }
+
+// storage format of the three-pass kernels: 0 = binary64, 1 = binary32 deviation
+int sprec(const lbm_problem *p) { return p->opt.precision == LBM_FP64 ? 0 : 1; }
 
 void *dev_alloc(lbm_problem *p, size_t bytes)
 {
@@ -97,6 +99,19 @@ double pr_alpha(double a, double b, double omega, double T, double R)
     return s * s;
 }
 
+void refresh_float_params(Params &P)
+{
+    P.fRT = (float)P.RT;
+    P.flnRT = (float)P.lnRT;
+    for (int i = 0; i < kMaxNc; ++i) {
+        P.fb[i] = (float)P.b[i];
+        P.finvM[i] = (float)P.invM[i];
+        P.fsqk[i] = (float)P.sqk[i];
+        P.frhobar[i] = (float)P.rhobar[i];
+    }
+    for (int k = 0; k < kMaxNc * kMaxNc; ++k) P.fA[k] = (float)P.A[k];
+}
+
 void build_params(lbm_problem *p)
 {
     Params &P = p->P;
@@ -120,6 +135,7 @@ void build_params(lbm_problem *p)
     for (int i = 0; i < p->nc; ++i)
         for (int j = 0; j < p->nc; ++j)
             P.A[i * kMaxNc + j] = std::sqrt(aa[i] * aa[j]) * (1.0 - p->kij[i * kMaxNc + j]);
+    refresh_float_params(P);
 }
 
 int ensure_allocated(lbm_problem *p)
@@ -139,34 +155,49 @@ int ensure_allocated(lbm_problem *p)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int sched = p->opt.schedule;
-    const bool can_fuse = fused_supported(p->lattice, p->nc);
+    const bool can_fuse = fused_supported(p->lattice, p->opt.precision, p->nc);
     if (sched == LBM_SCHED_FUSED && !can_fuse) return LBM_ENOTSUP;
     p->fused = can_fuse && sched != LBM_SCHED_THREEPASS;
-    const size_t sb = (size_t)pstore_bytes(p);
-    const size_t gb = (size_t)p->nc * p->Q * p->N * sb;
-    const size_t fb = (size_t)p->nc * p->N * sizeof(double);
-    p->g[0] = dev_alloc(p, gb);
-    p->g[1] = dev_alloc(p, gb);
+    const bool f32 = p->opt.precision != LBM_FP64;
+    const size_t nf = (size_t)p->nc * p->N;  // one field per component
+    for (int k = 0; k < 2; ++k) {
+        if (f32) {
+            p->st[k].g = dev_alloc(p, nf * (p->Q - 1) * sizeof(float));
+            p->st[k].rhi = dev_alloc(p, nf * sizeof(float));
+            p->st[k].rlo = (float *)dev_alloc(p, nf * sizeof(float));
+            if (!p->st[k].g || !p->st[k].rhi || !p->st[k].rlo) return LBM_ENOMEM;
+        } else {
+            p->st[k].g = dev_alloc(p, nf * p->Q * sizeof(double));
+            if (!p->st[k].g) return LBM_ENOMEM;
+            if (p->fused) {
+                p->st[k].rhi = dev_alloc(p, nf * sizeof(double));
+                if (!p->st[k].rhi) return LBM_ENOMEM;
+            }
+        }
+    }
+    const size_t fb = nf * sizeof(double);
     p->w.rho = (double *)dev_alloc(p, fb);
     p->w.lnf = (double *)dev_alloc(p, fb);
     p->w.psi = (double *)dev_alloc(p, (size_t)p->N * sizeof(double));
     p->w.lap = (double *)dev_alloc(p, (size_t)p->N * sizeof(double));
     p->w.jm = (double *)dev_alloc(p, (size_t)p->D * p->N * sizeof(double));
+    if (f32) {
+        p->w.osum = (float *)dev_alloc(p, nf * sizeof(float));
+        p->w.ocmp = (float *)dev_alloc(p, nf * sizeof(float));
+        if (!p->w.osum || !p->w.ocmp) return LBM_ENOMEM;
+    }
     p->partials = (double *)dev_alloc(p, (size_t)kReduceBlocks * p->nc * sizeof(double));
     p->res = (double *)dev_alloc(p, 64 * sizeof(double));
     p->flag = (int *)dev_alloc(p, 16);
     p->mon = (double *)dev_alloc(p, kMaxNc * sizeof(double));
-    if (!p->mon || !p->g[0] || !p->g[1] || !p->w.rho || !p->w.lnf || !p->w.psi || !p->w.lap || !p->w.jm ||
+    if (!p->mon || !p->w.rho || !p->w.lnf || !p->w.psi || !p->w.lap || !p->w.jm ||
         !p->partials || !p->res || !p->flag)
         return LBM_ENOMEM;
     if (p->fused) {
         p->geo = fused_geometry(p->opt.precision, p->nc, p->P, nsm);
-        const size_t rb = (size_t)p->nc * p->N * sb;
-        p->rs[0] = dev_alloc(p, rb);
-        p->rs[1] = dev_alloc(p, rb);
         p->mass_partials =
             (double *)dev_alloc(p, (size_t)p->geo.nstrips * p->geo.segs * p->nc * sizeof(double));
-        if (!p->rs[0] || !p->rs[1] || !p->mass_partials) return LBM_ENOMEM;
+        if (!p->mass_partials || p->geo.nstrips < 1) return LBM_ENOMEM;
     }
     if (cudaMemsetAsync(p->flag, 0, 16, p->stream) != cudaSuccess) return LBM_ECUDA;
     p->allocated = true;
@@ -180,29 +211,14 @@ int finish_init(lbm_problem *p)
     p->have_snap = false;
     p->monitor_step = -1;
     if (cudaMemsetAsync(p->flag, 0, 16, p->stream) != cudaSuccess) return LBM_ECUDA;
-    if (p->fused) {
-        int e = launch_fused_density(p->opt.precision, p->nc, p->P, p->g[0], p->rs[0], p->stream);
+    if (p->fused && p->opt.precision == LBM_FP64) {
+        int e = launch_fused_density(p->opt.precision, p->nc, p->P, p->st[0], p->stream);
         if (e) return LBM_ECUDA;
         p->launches += 1;
     }
     p->initialized = true;
     p->sticky = LBM_OK;
     return cuda_status(cudaGetLastError());
-}
-
-// mean density per component over the field (deviation storage reference)
-int set_rhobar(lbm_problem *p, const double *d_rho)
-{
-    if (p->opt.precision != LBM_FP32DEV) return LBM_OK;
-    int e = launch_mass(p->nc, p->N, d_rho, p->partials, p->res, p->flag, p->stream);
-    if (e) return LBM_ECUDA;
-    double m[kMaxNc];
-    if (cudaMemcpyAsync(m, p->res, p->nc * sizeof(double), cudaMemcpyDeviceToHost, p->stream) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(p->stream) != cudaSuccess)
-        return LBM_ECUDA;
-    for (int i = 0; i < p->nc; ++i) p->P.rhobar[i] = m[i] / (double)p->N;
-    return LBM_OK;
 }
 
 int check_flag(lbm_problem *p)
@@ -281,7 +297,8 @@ int lbm_set_options(lbm_problem *p, const lbm_options *opt)
 {
     if (!p || !opt) return LBM_EINVAL;
     if (p->allocated) return LBM_ESTATE;
-    if (opt->precision != LBM_FP64 && opt->precision != LBM_FP32DEV) return LBM_EINVAL;
+    if (opt->precision != LBM_FP64 && opt->precision != LBM_FP32DEV && opt->precision != LBM_FP32)
+        return LBM_EINVAL;
     if (opt->schedule < LBM_SCHED_AUTO || opt->schedule > LBM_SCHED_FUSED) return LBM_EINVAL;
     if (!(opt->kappa_ref >= 0.0) || !std::isfinite(opt->kappa_ref)) return LBM_EINVAL;
     if (opt->kappa_ref_index < 0 || opt->kappa_ref_index >= p->nc) return LBM_EINVAL;
@@ -301,9 +318,8 @@ int lbm_init_fields_device(lbm_problem *p, const double *d_rho, const double *d_
     if (!p || !d_rho) return LBM_EINVAL;
     int st = ensure_allocated(p);
     if (st) return st;
-    st = set_rhobar(p, d_rho);
-    if (st) return st;
-    if (launch_init_equilibrium(p->lattice, p->opt.precision, p->nc, p->P, d_rho, d_u, p->g[0],
+    p->launches += 1;
+    if (launch_init_equilibrium(p->lattice, sprec(p), p->nc, p->P, d_rho, d_u, p->st[0],
                                 p->stream))
         return LBM_ECUDA;
     return finish_init(p);
@@ -345,18 +361,17 @@ int lbm_step(lbm_problem *p, long long n)
         const bool mon = every > 0 && ((p->steps + 1) % every == 0);
         int e;
         if (p->fused) {
-            e = launch_fused_step(p->opt.precision, p->nc, p->P, p->geo, p->g[p->cur],
-                                  p->g[p->cur ^ 1], p->rs[p->cur], p->rs[p->cur ^ 1],
-                                  mon ? p->mass_partials : nullptr, p->stream);
+            e = launch_fused_step(p->opt.precision, p->nc, p->P, p->geo, p->st[p->cur],
+                                  p->st[p->cur ^ 1], mon ? p->mass_partials : nullptr, p->stream);
             p->launches += 1;
             if (!e && mon) {
                 e = launch_fused_mass_final(p->nc, p->geo, p->mass_partials, p->mon, p->flag, p->stream);
                 p->launches += 1;
             }
         } else {
-            e = launch_threepass_step(p->lattice, p->opt.precision, p->nc, p->P, p->g[p->cur],
-                                      p->g[p->cur ^ 1], p->w, p->stream);
-            p->launches += 3;
+            e = launch_threepass_step(p->lattice, sprec(p), p->nc, p->P, p->st[p->cur],
+                                      p->st[p->cur ^ 1], p->w, p->stream);
+            p->launches += threepass_launches_per_step(p->lattice, sprec(p), p->nc);
         }
         if (e) {
             p->sticky = LBM_ECUDA;
@@ -366,7 +381,7 @@ int lbm_step(lbm_problem *p, long long n)
         p->steps++;
         if (mon && !p->fused) {
             // mass of the new state: densities by the first pass of the next step's kernels
-            e = launch_fields(p->lattice, p->opt.precision, p->nc, p->P, p->g[p->cur], p->w, p->w.rho,
+            e = launch_fields(p->lattice, sprec(p), p->nc, p->P, p->st[p->cur], p->w, p->w.rho,
                               nullptr, nullptr, nullptr, p->stream);
             if (!e) e = launch_mass(p->nc, p->N, p->w.rho, p->partials, p->mon, p->flag, p->stream);
             p->launches += 3;
@@ -385,7 +400,7 @@ int lbm_moments_device(lbm_problem *p, double *d_rho, double *d_u, double *d_pre
     if (!p) return LBM_EINVAL;
     if (!p->initialized) return LBM_ESTATE;
     if (p->sticky) return p->sticky;
-    if (launch_fields(p->lattice, p->opt.precision, p->nc, p->P, p->g[p->cur], p->w, d_rho, d_u,
+    if (launch_fields(p->lattice, sprec(p), p->nc, p->P, p->st[p->cur], p->w, d_rho, d_u,
                       d_pressure, d_lnf, p->stream))
         return LBM_ECUDA;
     return LBM_OK;
@@ -421,7 +436,7 @@ int lbm_mass(lbm_problem *p, double *mass)
     if (!p || !mass) return LBM_EINVAL;
     if (!p->initialized) return LBM_ESTATE;
     if (p->sticky) return p->sticky;
-    if (launch_fields(p->lattice, p->opt.precision, p->nc, p->P, p->g[p->cur], p->w, p->w.rho,
+    if (launch_fields(p->lattice, sprec(p), p->nc, p->P, p->st[p->cur], p->w, p->w.rho,
                       nullptr, nullptr, nullptr, p->stream))
         return LBM_ECUDA;
     if (cudaMemsetAsync(p->flag, 0, sizeof(int), p->stream) != cudaSuccess) return LBM_ECUDA;
@@ -442,7 +457,7 @@ int lbm_convergence(lbm_problem *p, double *max_abs_drho)
         p->snap = (double *)dev_alloc(p, fb);
         if (!p->snap) return LBM_ENOMEM;
     }
-    if (launch_fields(p->lattice, p->opt.precision, p->nc, p->P, p->g[p->cur], p->w, p->w.rho,
+    if (launch_fields(p->lattice, sprec(p), p->nc, p->P, p->st[p->cur], p->w, p->w.rho,
                       nullptr, nullptr, nullptr, p->stream))
         return LBM_ECUDA;
     if (cudaMemsetAsync(p->flag, 0, sizeof(int), p->stream) != cudaSuccess) return LBM_ECUDA;
@@ -485,7 +500,7 @@ int lbm_get_state(lbm_problem *p, double *buf, size_t *bytes)
     double *d = nullptr;
     if (cudaMalloc(&d, need) != cudaSuccess) return LBM_ENOMEM;
     int st = LBM_OK;
-    if (launch_state_to_f64(p->lattice, p->opt.precision, p->nc, p->P, p->g[p->cur], d, p->stream))
+    if (launch_state_to_f64(p->lattice, sprec(p), p->nc, p->P, p->st[p->cur], d, p->stream))
         st = LBM_ECUDA;
     if (!st && cudaMemcpyAsync(buf, d, need, cudaMemcpyDeviceToHost, p->stream) != cudaSuccess) st = LBM_ECUDA;
     if (!st && cudaStreamSynchronize(p->stream) != cudaSuccess) st = LBM_ECUDA;
@@ -506,16 +521,7 @@ int lbm_set_state(lbm_problem *p, const double *buf, size_t bytes)
     double *d = nullptr;
     if (cudaMalloc(&d, need) != cudaSuccess) return LBM_ENOMEM;
     if (cudaMemcpyAsync(d, buf, need, cudaMemcpyHostToDevice, p->stream) != cudaSuccess) st = LBM_ECUDA;
-    if (!st && p->opt.precision == LBM_FP32DEV) {
-        // reference densities from the state itself: rho_i = sum_a g_{a,i}
-        std::vector<double> m(p->nc, 0.0);
-        for (int i = 0; i < p->nc; ++i) {
-            double s = 0.0;
-            for (size_t k = (size_t)i * p->Q * p->N; k < (size_t)(i + 1) * p->Q * p->N; ++k) s += buf[k];
-            p->P.rhobar[i] = s / (double)p->N;
-        }
-    }
-    if (!st && launch_state_from_f64(p->lattice, p->opt.precision, p->nc, p->P, d, p->g[0], p->stream))
+    if (!st && launch_state_from_f64(p->lattice, sprec(p), p->nc, p->P, d, p->st[0], p->stream))
         st = LBM_ECUDA;
     if (!st && cudaStreamSynchronize(p->stream) != cudaSuccess) st = LBM_ECUDA;
     cudaFree(d);

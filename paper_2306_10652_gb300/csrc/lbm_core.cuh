@@ -68,6 +68,31 @@ struct Params {
     double sqk[kMaxNc];     // sqrt(kappa_i), Eq. (4) and Eq. (6)
     double rhobar[kMaxNc];  // reference density of the deviation storage
     double A[kMaxNc * kMaxNc];  // sqrt((a alpha)_i (a alpha)_j) (1 - delta_ij), Eq. (10)
+    // binary32 copies for kernels whose thermodynamics run in binary32
+    float fRT, flnRT;
+    float fb[kMaxNc], finvM[kMaxNc], fsqk[kMaxNc], frhobar[kMaxNc];
+    float fA[kMaxNc * kMaxNc];
+};
+
+// Parameter access in the arithmetic type E of a kernel.
+template <typename E> struct PV;
+template <> struct PV<double> {
+    __device__ static double A(const Params &P, int k) { return P.A[k]; }
+    __device__ static double b(const Params &P, int i) { return P.b[i]; }
+    __device__ static double RT(const Params &P) { return P.RT; }
+    __device__ static double lnRT(const Params &P) { return P.lnRT; }
+    __device__ static double sqk(const Params &P, int i) { return P.sqk[i]; }
+    __device__ static double invM(const Params &P, int i) { return P.invM[i]; }
+    __device__ static double rhobar(const Params &P, int i) { return P.rhobar[i]; }
+};
+template <> struct PV<float> {
+    __device__ static float A(const Params &P, int k) { return P.fA[k]; }
+    __device__ static float b(const Params &P, int i) { return P.fb[i]; }
+    __device__ static float RT(const Params &P) { return P.fRT; }
+    __device__ static float lnRT(const Params &P) { return P.flnRT; }
+    __device__ static float sqk(const Params &P, int i) { return P.fsqk[i]; }
+    __device__ static float invM(const Params &P, int i) { return P.finvM[i]; }
+    __device__ static float rhobar(const Params &P, int i) { return P.frhobar[i]; }
 };
 
 // ---------------------------------------------------------------------------
@@ -81,48 +106,72 @@ struct Params {
 //   Lr = ln[(1 + (1+sqrt2) B) / (1 + (1-sqrt2) B)],
 //   S_i = sum_j x_j (a alpha)_ij,
 // which is the printed equation regrouped (the two p's cancel, so it holds
-// for p <= 0 too).  Every operation is binary64.
+// for p <= 0 too).  Every operation is in the arithmetic type E.
 // ---------------------------------------------------------------------------
-template <int NC>
-__device__ __forceinline__ void pr_lnf(const Params &P, const double (&rm)[NC], double (&lnf)[NC],
-                                       double *p_out)
+template <int NC, typename E = double>
+__device__ __forceinline__ void pr_lnf(const Params &P, const E (&rm)[NC], E (&lnf)[NC], E *p_out)
 {
-    constexpr double kSqrt2 = 1.4142135623730951;
-    double rho = 0.0;
+    using V = PV<E>;
+    const E kSqrt2 = (E)1.4142135623730951;
+    E rho = 0;
 #pragma unroll
     for (int i = 0; i < NC; ++i) rho += rm[i];
-    const double inv = 1.0 / rho;
-    double x[NC];
+    const E inv = (E)1 / rho;
+    E x[NC];
 #pragma unroll
     for (int i = 0; i < NC; ++i) x[i] = rm[i] * inv;
-    double bm = 0.0;
+    E bm = 0;
 #pragma unroll
-    for (int i = 0; i < NC; ++i) bm = fma(x[i], P.b[i], bm);
-    double S[NC];
+    for (int i = 0; i < NC; ++i) bm = fma(x[i], V::b(P, i), bm);
+    E S[NC];
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
-        double s = 0.0;
+        E s = 0;
 #pragma unroll
-        for (int j = 0; j < NC; ++j) s = fma(P.A[i * kMaxNc + j], x[j], s);
+        for (int j = 0; j < NC; ++j) s = fma(V::A(P, i * kMaxNc + j), x[j], s);
         S[i] = s;
     }
-    double am = 0.0;
+    E am = 0;
 #pragma unroll
     for (int i = 0; i < NC; ++i) am = fma(x[i], S[i], am);
-    const double RT = P.RT;
-    const double B = bm * rho;
-    const double omB = 1.0 - B;
-    const double den = fma(B, 2.0 - B, 1.0);  // 1 + 2B - B^2
-    const double amr = am * rho / RT;
-    const double Zm1 = B / omB - amr / den;
-    const double Lr = log(fma(1.0 + kSqrt2, B, 1.0) / fma(1.0 - kSqrt2, B, 1.0));
-    const double C0 = P.lnRT - log(omB);
-    const double invbm = 1.0 / bm;
-    const double C1 = Zm1 * invbm + am * Lr * invbm * invbm / (2.0 * kSqrt2 * RT);
-    const double C2 = -Lr * invbm / (kSqrt2 * RT);
+    const E RT = V::RT(P);
+    const E B = bm * rho;
+    const E omB = (E)1 - B;
+    const E den = fma(B, (E)2 - B, (E)1);  // 1 + 2B - B^2
+    const E amr = am * rho / RT;
+    const E Zm1 = B / omB - amr / den;
+    const E Lr = log(fma((E)1 + kSqrt2, B, (E)1) / fma((E)1 - kSqrt2, B, (E)1));
+    const E C0 = V::lnRT(P) - log(omB);
+    const E invbm = (E)1 / bm;
+    const E C1 = Zm1 * invbm + am * Lr * invbm * invbm / ((E)2 * kSqrt2 * RT);
+    const E C2 = -Lr * invbm / (kSqrt2 * RT);
 #pragma unroll
-    for (int i = 0; i < NC; ++i) lnf[i] = log(rm[i]) + C0 + fma(P.b[i], C1, S[i] * C2);
+    for (int i = 0; i < NC; ++i) lnf[i] = log(rm[i]) + C0 + fma(V::b(P, i), C1, S[i] * C2);
     if (p_out) *p_out = RT * rho / omB - am * rho * rho / den;
+}
+
+// Error-free binary32 transformations (Knuth TwoSum, Dekker fast TwoSum).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bp = s - a;
+    e = (a - (s - bp)) + (b - bp);
+}
+// compensated accumulation (s, c) += x
+__device__ __forceinline__ void acc_add(float &s, float &c, float x)
+{
+    float e;
+    two_sum(s, x, s, e);
+    c += e;
+}
+// (hi, lo) + (s, c), renormalised
+__device__ __forceinline__ void pair_add(float &hi, float &lo, float s, float c)
+{
+    float h, e;
+    two_sum(hi, s, h, e);
+    const float l = lo + (e + c);
+    hi = h + l;
+    lo = l - (hi - h);
 }
 
 // periodic neighbour index

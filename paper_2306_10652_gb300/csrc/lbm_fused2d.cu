@@ -1,27 +1,100 @@
-// lbm_fused2d.cu -- single-pass D2Q9 time step (not built yet: the library
-// reports it unsupported and runs the three-pass schedule).
-#include "lbm_internal.h"
+// lbm_fused2d.cu -- dispatch, launch geometry and reductions of the fused
+// single-pass D2Q9 schedule; the kernels are instantiated in lbm_fz_*.cu.
+#include "lbm_fused2d.cuh"
 
 namespace lbmfug {
+namespace fz {
+const Ops *f64_lo(int nc);
+const Ops *f64_hi(int nc);
+const Ops *f32d_lo(int nc);
+const Ops *f32d_hi(int nc);
+const Ops *f32f_lo(int nc);
+const Ops *f32f_hi(int nc);
+}  // namespace fz
 
-bool fused_supported(int, int) { return false; }
+namespace {
 
-FusedGeom fused_geometry(int, int, const Params &, int) { return FusedGeom{}; }
-
-int launch_fused_density(int, int, const Params &, const void *, void *, cudaStream_t)
+// prec: 0 = binary64 storage and arithmetic; 1 = binary32 deviation storage
+// with binary64 thermodynamics and forces; 2 = binary32 throughout.
+const fz::Ops *lookup(int prec, int nc)
 {
-    return (int)cudaErrorNotSupported;
+    if (nc < 1 || nc > kMaxNc) return nullptr;
+    const bool lo = nc <= 8;
+    switch (prec) {
+    case 0: return lo ? fz::f64_lo(nc) : fz::f64_hi(nc);
+    case 1: return lo ? fz::f32d_lo(nc) : fz::f32d_hi(nc);
+    case 2: return lo ? fz::f32f_lo(nc) : fz::f32f_hi(nc);
+    default: return nullptr;
+    }
 }
 
-int launch_fused_step(int, int, const Params &, const FusedGeom &, const void *, void *,
-                      const void *, void *, double *, cudaStream_t)
+size_t max_optin_smem()
 {
-    return (int)cudaErrorNotSupported;
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return 48 * 1024;
+    return (size_t)v;
 }
 
-int launch_fused_mass_final(int, const FusedGeom &, const double *, double *, int *, cudaStream_t)
+__global__ void k_mass_final(int nc, int nblocks, const double *__restrict__ partials,
+                             double *__restrict__ out, int *__restrict__ nonfinite)
 {
-    return (int)cudaErrorNotSupported;
+    const int i = threadIdx.x;
+    if (i >= nc) return;
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += partials[(long long)b * nc + i];
+    out[i] = s;
+    if (!isfinite(s)) atomicExch(nonfinite, 1);
+}
+
+}  // namespace
+
+bool fused_supported(int lat, int prec, int nc)
+{
+    if (lat != 0) return false;
+    const fz::Ops *o = lookup(prec, nc);
+    return o && o->smem(fz::kWmax) <= max_optin_smem();
+}
+
+FusedGeom fused_geometry(int prec, int nc, const Params &P, int num_sms)
+{
+    FusedGeom g{};
+    const fz::Ops *o = lookup(prec, nc);
+    if (!o) return g;
+    g.threads = fz::kT;
+    g.nstrips = (P.nx + fz::kWmax - 1) / fz::kWmax;
+    g.strip = (P.nx + g.nstrips - 1) / g.nstrips;   // balanced strip width <= kWmax
+    g.smem = o->smem(g.strip);
+    int per_sm = o->occupancy(g.smem);
+    if (per_sm < 1) per_sm = 1;
+    const long long slots = (long long)num_sms * per_sm;
+    long long segs = slots / g.nstrips;
+    if (segs < 1) segs = 1;
+    if (segs > P.ny) segs = P.ny;
+    g.seg_h = (int)((P.ny + segs - 1) / segs);
+    g.segs = (P.ny + g.seg_h - 1) / g.seg_h;
+    return g;
+}
+
+int launch_fused_density(int prec, int nc, const Params &P, StateBufs st, cudaStream_t s)
+{
+    const fz::Ops *o = lookup(prec, nc);
+    return o ? o->density(P, st, s) : (int)cudaErrorInvalidValue;
+}
+
+int launch_fused_step(int prec, int nc, const Params &P, const FusedGeom &geo, StateBufs in,
+                      StateBufs out, double *mass_partials, cudaStream_t s)
+{
+    const fz::Ops *o = lookup(prec, nc);
+    return o ? o->step(P, geo, in, out, mass_partials, s) : (int)cudaErrorInvalidValue;
+}
+
+int launch_fused_mass_final(int nc, const FusedGeom &geo, const double *partials, double *out,
+                            int *nonfinite, cudaStream_t s)
+{
+    k_mass_final<<<1, 32, 0, s>>>(nc, geo.nstrips * geo.segs, partials, out, nonfinite);
+    return (int)cudaGetLastError();
 }
 
 }  // namespace lbmfug

@@ -1,0 +1,732 @@
+// lbm_fused2d.cuh -- single-pass D2Q9 time step.
+//
+// One launch per step.  The state is the post-streaming population set g(t)
+// (Eq. 1a) plus the density state R(t) = sum_a g_{a,i}(t) per node and
+// component, which the previous step produced on chip.  Each CTA owns a strip
+// of W interior columns (one thread per column, plus one halo column on each
+// side) and a segment of H rows, which it walks row by row:
+//
+//   row k   : load R(k) on columns [-3, W+3) -> psi(k) = sum_j sqrt(kappa_j) rho~_j
+//   row k-1 : ln f_i (Eqs. 9-12) and mu_i = RT ln f_i - sqrt(kappa_i) lap psi
+//             on columns [-2, W+2)   (Eq. 5 with Eq. 4: sum_j kappa_ij lap rho~_j
+//             = sqrt(kappa_i) lap psi)
+//   row k-2 : F_i = -rho~_i grad mu_i, grad rho_i, u = (sum e g + F/2)/rho,
+//             equilibrium (Eq. 1b), forcing (Eq. 1c), BGK (Eq. 1a) on columns
+//             [-1, W+1); push streaming of the interior columns to g(t+1);
+//             the new densities R(t+1) of the interior are gathered from the
+//             collided values of rows k-3..k-1 and columns -1..W in a fixed
+//             order (no atomics), so R(t+1) needs no second pass over g.
+//
+// DRAM traffic per node-step: g read + g written (the algorithmic bytes) plus
+// R read + R written (Nc values each); halo rows and columns come from L2.
+// Storage S (double, or float deviation h = g - delta_a0 rhobar_i), EOS and
+// force arithmetic E (double or float), collision arithmetic S.
+#pragma once
+
+#include "lbm_internal.h"
+
+namespace lbmfug {
+namespace fz {
+
+constexpr int kT = 128;     // threads per CTA: one column each
+constexpr int kWmax = kT - 2;
+
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+template <int NC, typename S, typename E> struct Smem {
+    static __host__ __device__ constexpr size_t rs(int W) { return align16((size_t)4 * NC * (W + 6) * sizeof(S)); }
+    static __host__ __device__ constexpr size_t ps(int W) { return align16((size_t)3 * (W + 6) * sizeof(E)); }
+    static __host__ __device__ constexpr size_t mu(int W) { return align16((size_t)3 * NC * (W + 4) * sizeof(E)); }
+    static __host__ __device__ constexpr size_t xc() { return align16((size_t)6 * NC * kT * sizeof(S)); }
+    static __host__ __device__ constexpr size_t red() { return align16((size_t)(kT / 32) * NC * sizeof(double)); }
+    static __host__ __device__ constexpr size_t total(int W) { return rs(W) + ps(W) + mu(W) + xc() + red(); }
+};
+
+__device__ __forceinline__ int wrapc(int v, int n)
+{
+    if (v >= 0 && v < n) return v;
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+template <int NC, typename S, typename E>
+__global__ void __launch_bounds__(kT)
+    k_fused(const Params P, const int W, const int H, const S *__restrict__ gin,
+            S *__restrict__ gout, const S *__restrict__ rin, S *__restrict__ rout,
+            double *__restrict__ mass_partials)
+{
+    using L = Lattice<0>;
+    using V = PV<E>;
+    using VS = PV<S>;
+    constexpr bool kDev = sizeof(S) == 4;                 // deviation storage
+    constexpr bool kKeep = 9 * NC * sizeof(S) <= 360;     // populations held in registers
+    extern __shared__ __align__(16) unsigned char smem[];
+    using SM = Smem<NC, S, E>;
+    S *RS = (S *)smem;                                   // [4][NC][W+6]  R rows
+    E *PS = (E *)(smem + SM::rs(W));                     // [3][W+6]      psi rows
+    E *MU = (E *)(smem + SM::rs(W) + SM::ps(W));         // [3][NC][W+4]  mu rows
+    S *XC = (S *)(smem + SM::rs(W) + SM::ps(W) + SM::mu(W));  // [6][NC][kT] exchange
+    double *RED = (double *)(smem + SM::rs(W) + SM::ps(W) + SM::mu(W) + SM::xc());
+
+    const int nx = P.nx, ny = P.ny;
+    const long long N = P.N;
+    const int CW = W + 6, CM = W + 4;
+    const int x0 = blockIdx.x * W;
+    const int w = min(W, nx - x0);
+    const int y0 = blockIdx.y * H;
+    const int h = min(H, ny - y0);
+    const int t = threadIdx.x;
+    const int col = t - 1;                 // collision column of this thread
+    const bool active = t < w + 2;         // columns -1 .. w
+    const bool interior = col >= 0 && col < w;
+    const int xg = wrapc(x0 + col, nx);
+    const int xd[3] = {wrapc(xg - 1, nx), xg, wrapc(xg + 1, nx)};  // destination columns, ex = -1, 0, 1
+    // phase (A) columns of this thread: c = t - 3 and c = t - 3 + kT
+    const int cA0 = t - 3, cA1 = t - 3 + kT;
+    const bool hasA0 = cA0 < w + 3, hasA1 = cA1 < w + 3;
+    const int xA0 = wrapc(x0 + cA0, nx), xA1 = hasA1 ? wrapc(x0 + cA1, nx) : 0;
+    const E RT = V::RT(P);
+    const S om = (S)P.omega, cF = (S)(1.0 - 0.5 * P.omega);
+
+    S msum[NC], mcmp[NC];      // per-thread mass of the written rows (compensated)
+    S accA[NC], accB[NC];
+    S rp0[NC], rp1[NC];        // prefetched density state of the next row
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+        msum[i] = 0;
+        mcmp[i] = 0;
+        accA[i] = 0;
+        accB[i] = 0;
+    }
+    {
+        const long long rowb = (long long)wrapc(y0 - 3, ny) * nx;
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+            rp0[i] = hasA0 ? __ldg(rin + i * N + rowb + xA0) : (S)0;
+            rp1[i] = hasA1 ? __ldg(rin + i * N + rowb + xA1) : (S)0;
+        }
+    }
+
+    const int nrows = h + 6;  // rows y0-3 .. y0+h+2
+    for (int kk = 0; kk < nrows; ++kk) {
+        const int k = y0 - 3 + kk;
+        // ---- (0) populations of the collision row k-2, in flight during (A), (B) ----
+        const int crow = k - 2;
+        const int yc = wrapc(crow, ny);
+        const long long rc = (long long)yc * nx + xg;
+        S hv[kKeep ? NC : 1][9];
+        if (kKeep && kk >= 4 && active) {
+#pragma unroll
+            for (int i = 0; i < NC; ++i)
+#pragma unroll
+                for (int a = 0; a < 9; ++a) hv[kKeep ? i : 0][a] = __ldg(gin + (i * 9 + a) * N + rc);
+        }
+        // ---- (A) density state and psi of row k --------------------------------
+        {
+            const int s4 = kk & 3, s3 = kk % 3;
+            if (hasA0) {
+                E ps = 0;
+#pragma unroll
+                for (int i = 0; i < NC; ++i) {
+                    RS[(s4 * NC + i) * CW + cA0 + 3] = rp0[i];
+                    ps = fma(V::sqk(P, i), (V::rhobar(P, i) + (E)rp0[i]) * V::invM(P, i), ps);
+                }
+                PS[s3 * CW + cA0 + 3] = ps;
+            }
+            if (hasA1) {
+                E ps = 0;
+#pragma unroll
+                for (int i = 0; i < NC; ++i) {
+                    RS[(s4 * NC + i) * CW + cA1 + 3] = rp1[i];
+                    ps = fma(V::sqk(P, i), (V::rhobar(P, i) + (E)rp1[i]) * V::invM(P, i), ps);
+                }
+                PS[s3 * CW + cA1 + 3] = ps;
+            }
+        }
+        __syncthreads();
+        // ---- (B) ln f and mu of row k-1 ------------------------------------------
+        if (kk >= 2) {
+            const int q = kk - 1;
+            const int s4 = q & 3;
+            const E *p0 = PS + ((q + 2) % 3) * CW;  // row q-1
+            const E *p1 = PS + (q % 3) * CW;        // row q
+            const E *p2 = PS + ((q + 1) % 3) * CW;  // row q+1
+            for (int c = t - 2; c < w + 2; c += kT) {
+                const int cc = c + 3;
+                E rm[NC], lf[NC];
+#pragma unroll
+                for (int i = 0; i < NC; ++i)
+                    rm[i] = (V::rhobar(P, i) + (E)RS[(s4 * NC + i) * CW + cc]) * V::invM(P, i);
+                pr_lnf<NC, E>(P, rm, lf, nullptr);
+                const E c0 = p1[cc];
+                const E faces = (p1[cc + 1] - c0) + (p1[cc - 1] - c0) + (p2[cc] - c0) + (p0[cc] - c0);
+                const E diags = (p2[cc + 1] - c0) + (p0[cc - 1] - c0) + (p0[cc + 1] - c0) + (p2[cc - 1] - c0);
+                const E lap = (E)6 * fma((E)(1.0 / 9.0), faces, (E)(1.0 / 36.0) * diags);
+#pragma unroll
+                for (int i = 0; i < NC; ++i)
+                    MU[((q % 3) * NC + i) * CM + c + 2] = fma(RT, lf[i], -V::sqk(P, i) * lap);
+            }
+        }
+        __syncthreads();
+        // ---- prefetch the density state of row k+1 (in flight during (C)) ---------
+        if (kk + 1 < nrows) {
+            const long long rowb = (long long)wrapc(k + 1, ny) * nx;
+#pragma unroll
+            for (int i = 0; i < NC; ++i) {
+                if (hasA0) rp0[i] = __ldg(rin + i * N + rowb + xA0);
+                if (hasA1) rp1[i] = __ldg(rin + i * N + rowb + xA1);
+            }
+        }
+        if (kk < 4) continue;
+        // ---- (C) collision of row k-2 --------------------------------------------
+        const int q = kk - 2;
+        const bool own_row = crow >= y0 && crow < y0 + h;
+        S ownv[3][NC];  // collided values with dx = 0, by dy = -1, 0, +1
+        if (active) {
+            const long long yd[3] = {(long long)wrapc(yc - 1, ny) * nx, (long long)yc * nx,
+                                     (long long)wrapc(yc + 1, ny) * nx};
+            const int cc = col + 3, cm = col + 2;
+            const S *R0 = RS + ((q + 3) & 3) * NC * CW;  // row q-1
+            const S *R1 = RS + (q & 3) * NC * CW;        // row q
+            const S *R2 = RS + ((q + 1) & 3) * NC * CW;  // row q+1
+            const E *M0 = MU + ((q + 2) % 3) * NC * CM;
+            const E *M1 = MU + (q % 3) * NC * CM;
+            const E *M2 = MU + ((q + 1) % 3) * NC * CM;
+            // momentum sum_i sum_a e_a g_{a,i}
+            S jx = 0, jy = 0;
+#pragma unroll
+            for (int i = 0; i < NC; ++i) {
+                S v[9];
+#pragma unroll
+                for (int a = 0; a < 9; ++a)
+                    v[a] = kKeep ? hv[kKeep ? i : 0][a] : __ldg(gin + (i * 9 + a) * N + rc);
+                jx += (v[1] - v[2]) + (v[5] - v[6]) + (v[7] - v[8]);
+                jy += (v[3] - v[4]) + (v[5] - v[6]) + (v[8] - v[7]);
+            }
+            // Eq. (5): F_i = -rho~_i grad mu_i
+            S Fx[NC], Fy[NC];
+            E Fsx = 0, Fsy = 0, rt = 0;
+#pragma unroll
+            for (int i = 0; i < NC; ++i) {
+                const E *m0 = M0 + i * CM, *m1 = M1 + i * CM, *m2 = M2 + i * CM;
+                // grad X = 3 sum_pairs w e (X(r+e) - X(r-e)): faces 1/9, diagonals 1/36
+                const E dE = m1[cm + 1] - m1[cm - 1];
+                const E dN = m2[cm] - m0[cm];
+                const E dNE = m2[cm + 1] - m0[cm - 1];
+                const E dSE = m0[cm + 1] - m2[cm - 1];
+                const E gx = (E)3 * fma((E)(1.0 / 9.0), dE, (E)(1.0 / 36.0) * (dNE + dSE));
+                const E gy = (E)3 * fma((E)(1.0 / 9.0), dN, (E)(1.0 / 36.0) * (dNE - dSE));
+                const E ri = V::rhobar(P, i) + (E)R1[i * CW + cc];
+                rt += ri;
+                const E rmi = ri * V::invM(P, i);
+                const E fx = -rmi * gx, fy = -rmi * gy;
+                Fsx += fx;
+                Fsy += fy;
+                Fx[i] = (S)fx;
+                Fy[i] = (S)fy;
+            }
+            const E irt = (E)1 / rt;
+            const S ux = (S)(fma((E)0.5, Fsx, (E)jx) * irt);
+            const S uy = (S)(fma((E)0.5, Fsy, (E)jy) * irt);
+            const S u2 = ux * ux + uy * uy;
+            // per-direction scalars (component independent)
+            S ue[9], Bq[9], c9[9];
+#pragma unroll
+            for (int a = 0; a < 9; ++a) {
+                ue[a] = (S)L::e(a, 0) * ux + (S)L::e(a, 1) * uy;
+                Bq[a] = ue[a] * fma((S)4.5, ue[a], (S)3) - (S)1.5 * u2;
+                c9[a] = fma((S)9, ue[a], (S)3);
+            }
+#pragma unroll
+            for (int i = 0; i < NC; ++i) {
+                const S *r0 = R0 + i * CW, *r1 = R1 + i * CW, *r2 = R2 + i * CW;
+                const S dE = r1[cc + 1] - r1[cc - 1];
+                const S dN = r2[cc] - r0[cc];
+                const S dNE = r2[cc + 1] - r0[cc - 1];
+                const S dSE = r0[cc + 1] - r2[cc - 1];
+                const S Gx = (S)3 * fma((S)(1.0 / 9.0), dE, (S)(1.0 / 36.0) * (dNE + dSE));
+                const S Gy = (S)3 * fma((S)(1.0 / 9.0), dN, (S)(1.0 / 36.0) * (dNE - dSE));
+                const S dri = r1[cc];                          // rho_i - rhobar_i
+                const S ri = VS::rhobar(P, i) + dri;
+                const S Fu3 = (S)3 * (Fx[i] * ux + Fy[i] * uy);
+                const S Gu = Gx * ux + Gy * uy;
+                S v[9];
+#pragma unroll
+                for (int a = 0; a < 9; ++a)
+                    v[a] = kKeep ? hv[kKeep ? i : 0][a] : __ldg(gin + (i * 9 + a) * N + rc);
+                S others = 0;  // sum of the moving populations of this node
+                if (kDev)
+#pragma unroll
+                    for (int a = 1; a < 9; ++a) others += v[a];
+#pragma unroll
+                for (int a = 0; a < 9; ++a) {
+                    const int ex = L::e(a, 0), ey = L::e(a, 1);
+                    const S wa = (S)L::w(a);
+                    const S Fe = (S)ex * Fx[i] + (S)ey * Fy[i];
+                    const S Ge = (S)ex * Gx + (S)ey * Gy;
+                    const S cW = (S)(0.5 * (3.0 * (ex * ex + ey * ey) - 2.0) - 1.0);
+                    // Eq. (1c): F.[(e-u)/cs2 + (u.e)e/cs4] + grad rho.[-u + (u.e)e/cs2 + (e^2/cs2 - D)u/2]
+                    const S Fa = wa * (fma(Fe, c9[a], -Fu3) + fma((S)3 * ue[a], Ge, cW * Gu));
+                    S gs;
+                    if (kDev && a == 0) {
+                        // Eq. (1a) at rest with Eq. (1b): h0 + w (sum_a h_a - h0 + w0 rho B0) + cF F0,
+                        // the node's own populations carrying its mass exactly
+                        gs = v[0] + fma(om, others + wa * ri * Bq[0], cF * Fa);
+                    } else {
+                        const S geq = wa * ri * Bq[a] + (a == 0 ? dri : (S)0);
+                        gs = fma(om, geq - v[a], v[a]) + cF * Fa;
+                    }
+                    if (interior && own_row) gout[(i * 9 + a) * N + yd[ey + 1] + xd[ex + 1]] = gs;
+                    if (ex == 0)
+                        ownv[ey + 1][i] = gs;
+                    else
+                        XC[(((ey + 1) * 2 + (ex > 0 ? 0 : 1)) * NC + i) * kT + t] = gs;
+                }
+            }
+        }
+        __syncthreads();
+        // ---- gather R(t+1) of the interior columns ---------------------------------
+        if (interior) {
+            const bool write_row = (crow - 1) >= y0 && (crow - 1) < y0 + h;
+            const long long rw = (long long)wrapc(crow - 1, ny) * nx + xg;
+#pragma unroll
+            for (int i = 0; i < NC; ++i) {
+                S Pd[3];
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy)
+                    Pd[dy] = (XC[((dy * 2 + 0) * NC + i) * kT + t - 1] + ownv[dy][i]) +
+                             XC[((dy * 2 + 1) * NC + i) * kT + t + 1];
+                accA[i] += Pd[0];  // row crow-1 now complete
+                if (write_row) {
+                    rout[i * N + rw] = accA[i];
+                    // compensated (Kahan) running sum of the written densities
+                    const S yv = accA[i] - mcmp[i];
+                    const S tv = msum[i] + yv;
+                    mcmp[i] = (tv - msum[i]) - yv;
+                    msum[i] = tv;
+                }
+                accA[i] = accB[i] + Pd[1];
+                accB[i] = Pd[2];
+            }
+        }
+    }
+    if (mass_partials) {
+        // deterministic block reduction of the mass of the rows written
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+            double v = (double)msum[i] - (double)mcmp[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if ((t & 31) == 0) RED[(t >> 5) * NC + i] = v;
+        }
+        __syncthreads();
+        if (t < NC) {
+            double s = 0.0;
+            for (int wv = 0; wv < kT / 32; ++wv) s += RED[wv * NC + t];
+            s += P.rhobar[t] * (double)w * (double)h;
+            mass_partials[((long long)blockIdx.y * gridDim.x + blockIdx.x) * NC + t] = s;
+        }
+    }
+}
+
+template <int NC, typename E> struct Smem32 {
+    static __host__ __device__ constexpr size_t rs(int W) { return align16((size_t)4 * NC * (W + 6) * sizeof(float)); }
+    static __host__ __device__ constexpr size_t ps(int W) { return align16((size_t)3 * (W + 6) * sizeof(E)); }
+    static __host__ __device__ constexpr size_t mu(int W) { return align16((size_t)3 * NC * (W + 4) * sizeof(E)); }
+    static __host__ __device__ constexpr size_t xc() { return align16((size_t)6 * NC * kT * sizeof(float)); }
+    static __host__ __device__ constexpr size_t red() { return align16((size_t)(kT / 32) * NC * sizeof(double)); }
+    static __host__ __device__ constexpr size_t total(int W) { return 2 * rs(W) + ps(W) + mu(W) + xc() + red(); }
+};
+
+// Binary32 state: the 8 moving populations g[i][a-1][node] (a = 1..8) and the
+// density rho_i = hi + lo.  Collision arithmetic in binary32; thermodynamics
+// and forces in E.  The new density of a node is its old density minus the
+// populations that left it plus those that arrived, all compensated sums of
+// the stored binary32 values, so the component mass is conserved to the
+// rounding of the pair.
+template <int NC, typename E>
+__global__ void __launch_bounds__(kT)
+    k_fused32(const Params P, const int W, const int H, StateBufs in, StateBufs out,
+              double *__restrict__ mass_partials)
+{
+    using L = Lattice<0>;
+    using V = PV<E>;
+    constexpr bool kKeep = 8 * NC * sizeof(float) <= 352;  // moving populations held in registers
+    extern __shared__ __align__(16) unsigned char smem[];
+    using SM = Smem32<NC, E>;
+    float *RS = (float *)smem;                                 // [4][NC][W+6] rho hi rows
+    float *RL = (float *)(smem + SM::rs(W));                   // [4][NC][W+6] rho lo rows
+    E *PS = (E *)(smem + 2 * SM::rs(W));                       // [3][W+6]     psi rows
+    E *MU = (E *)(smem + 2 * SM::rs(W) + SM::ps(W));           // [3][NC][W+4] mu rows
+    float *XC = (float *)(smem + 2 * SM::rs(W) + SM::ps(W) + SM::mu(W));  // [6][NC][kT]
+    double *RED = (double *)(smem + 2 * SM::rs(W) + SM::ps(W) + SM::mu(W) + SM::xc());
+    const float *gin = (const float *)in.g;
+    float *gout = (float *)out.g;
+    const float *rhin = in.rhi_f();
+    const float *rlin = in.rlo;
+
+    const int nx = P.nx, ny = P.ny;
+    const long long N = P.N;
+    const int CW = W + 6, CM = W + 4;
+    const int x0 = blockIdx.x * W;
+    const int w = min(W, nx - x0);
+    const int y0 = blockIdx.y * H;
+    const int h = min(H, ny - y0);
+    const int t = threadIdx.x;
+    const int col = t - 1;
+    const bool active = t < w + 2;
+    const bool interior = col >= 0 && col < w;
+    const int xg = wrapc(x0 + col, nx);
+    const int xd[3] = {wrapc(xg - 1, nx), xg, wrapc(xg + 1, nx)};
+    const int cA0 = t - 3, cA1 = t - 3 + kT;
+    const bool hasA0 = cA0 < w + 3, hasA1 = cA1 < w + 3;
+    const int xA0 = wrapc(x0 + cA0, nx), xA1 = hasA1 ? wrapc(x0 + cA1, nx) : 0;
+    const E RT = V::RT(P);
+    const float om = (float)P.omega, cF = (float)(1.0 - 0.5 * P.omega);
+
+    float msum[NC], mcmp[NC];     // mass of the rows written (compensated)
+    float aS[NC], aC[NC], bS[NC], bC[NC];  // pending density updates of rows crow-1, crow
+    float rh0[NC], rh1[NC], rl0[NC], rl1[NC];  // prefetched density pair of the next row
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+        msum[i] = mcmp[i] = 0.0f;
+        aS[i] = aC[i] = bS[i] = bC[i] = 0.0f;
+    }
+    {
+        const long long rowb = (long long)wrapc(y0 - 3, ny) * nx;
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+            rh0[i] = hasA0 ? __ldg(rhin + i * N + rowb + xA0) : 0.0f;
+            rl0[i] = hasA0 ? __ldg(rlin + i * N + rowb + xA0) : 0.0f;
+            rh1[i] = hasA1 ? __ldg(rhin + i * N + rowb + xA1) : 0.0f;
+            rl1[i] = hasA1 ? __ldg(rlin + i * N + rowb + xA1) : 0.0f;
+        }
+    }
+
+    const int nrows = h + 6;
+    for (int kk = 0; kk < nrows; ++kk) {
+        const int k = y0 - 3 + kk;
+        const int crow = k - 2;
+        const int yc = wrapc(crow, ny);
+        const long long rc = (long long)yc * nx + xg;
+        float hv[kKeep ? NC : 1][8];
+        if (kKeep && kk >= 4 && active) {
+#pragma unroll
+            for (int i = 0; i < NC; ++i)
+#pragma unroll
+                for (int a = 0; a < 8; ++a) hv[kKeep ? i : 0][a] = __ldg(gin + (i * 8 + a) * N + rc);
+        }
+        // ---- (A) density pair and psi of row k ----------------------------------
+        {
+            const int s4 = kk & 3, s3 = kk % 3;
+            if (hasA0) {
+                E ps = 0;
+#pragma unroll
+                for (int i = 0; i < NC; ++i) {
+                    RS[(s4 * NC + i) * CW + cA0 + 3] = rh0[i];
+                    RL[(s4 * NC + i) * CW + cA0 + 3] = rl0[i];
+                    ps = fma(V::sqk(P, i), ((E)rh0[i] + (E)rl0[i]) * V::invM(P, i), ps);
+                }
+                PS[s3 * CW + cA0 + 3] = ps;
+            }
+            if (hasA1) {
+                E ps = 0;
+#pragma unroll
+                for (int i = 0; i < NC; ++i) {
+                    RS[(s4 * NC + i) * CW + cA1 + 3] = rh1[i];
+                    RL[(s4 * NC + i) * CW + cA1 + 3] = rl1[i];
+                    ps = fma(V::sqk(P, i), ((E)rh1[i] + (E)rl1[i]) * V::invM(P, i), ps);
+                }
+                PS[s3 * CW + cA1 + 3] = ps;
+            }
+        }
+        __syncthreads();
+        // ---- (B) ln f and mu of row k-1 ------------------------------------------
+        if (kk >= 2) {
+            const int q = kk - 1;
+            const int s4 = q & 3;
+            const E *p0 = PS + ((q + 2) % 3) * CW;
+            const E *p1 = PS + (q % 3) * CW;
+            const E *p2 = PS + ((q + 1) % 3) * CW;
+            for (int c = t - 2; c < w + 2; c += kT) {
+                const int cc = c + 3;
+                E rm[NC], lf[NC];
+#pragma unroll
+                for (int i = 0; i < NC; ++i)
+                    rm[i] = ((E)RS[(s4 * NC + i) * CW + cc] + (E)RL[(s4 * NC + i) * CW + cc]) * V::invM(P, i);
+                pr_lnf<NC, E>(P, rm, lf, nullptr);
+                const E c0 = p1[cc];
+                const E faces = (p1[cc + 1] - c0) + (p1[cc - 1] - c0) + (p2[cc] - c0) + (p0[cc] - c0);
+                const E diags = (p2[cc + 1] - c0) + (p0[cc - 1] - c0) + (p0[cc + 1] - c0) + (p2[cc - 1] - c0);
+                const E lap = (E)6 * fma((E)(1.0 / 9.0), faces, (E)(1.0 / 36.0) * diags);
+#pragma unroll
+                for (int i = 0; i < NC; ++i)
+                    MU[((q % 3) * NC + i) * CM + c + 2] = fma(RT, lf[i], -V::sqk(P, i) * lap);
+            }
+        }
+        __syncthreads();
+        if (kk + 1 < nrows) {
+            const long long rowb = (long long)wrapc(k + 1, ny) * nx;
+#pragma unroll
+            for (int i = 0; i < NC; ++i) {
+                if (hasA0) {
+                    rh0[i] = __ldg(rhin + i * N + rowb + xA0);
+                    rl0[i] = __ldg(rlin + i * N + rowb + xA0);
+                }
+                if (hasA1) {
+                    rh1[i] = __ldg(rhin + i * N + rowb + xA1);
+                    rl1[i] = __ldg(rlin + i * N + rowb + xA1);
+                }
+            }
+        }
+        if (kk < 4) continue;
+        // ---- (C) collision of row k-2 (moving populations only) --------------------
+        const int q = kk - 2;
+        const bool own_row = crow >= y0 && crow < y0 + h;
+        float ownv[3][NC];   // dx = 0 moving values by dy = -1, +1 (index 0, 2)
+        float oS[NC], oC[NC];  // what leaves this node
+        if (active) {
+            const long long yd[3] = {(long long)wrapc(yc - 1, ny) * nx, (long long)yc * nx,
+                                     (long long)wrapc(yc + 1, ny) * nx};
+            const int cc = col + 3, cm = col + 2;
+            const float *R0 = RS + ((q + 3) & 3) * NC * CW;
+            const float *R1 = RS + (q & 3) * NC * CW;
+            const float *R2 = RS + ((q + 1) & 3) * NC * CW;
+            const float *L1 = RL + (q & 3) * NC * CW;
+            const E *M0 = MU + ((q + 2) % 3) * NC * CM;
+            const E *M1 = MU + (q % 3) * NC * CM;
+            const E *M2 = MU + ((q + 1) % 3) * NC * CM;
+            float jx = 0.0f, jy = 0.0f;
+#pragma unroll
+            for (int i = 0; i < NC; ++i) {
+                float v[9];
+                v[0] = 0.0f;
+#pragma unroll
+                for (int a = 1; a < 9; ++a)
+                    v[a] = kKeep ? hv[kKeep ? i : 0][a - 1] : __ldg(gin + (i * 8 + a - 1) * N + rc);
+                jx += (v[1] - v[2]) + (v[5] - v[6]) + (v[7] - v[8]);
+                jy += (v[3] - v[4]) + (v[5] - v[6]) + (v[8] - v[7]);
+            }
+            float Fx[NC], Fy[NC];
+            E Fsx = 0, Fsy = 0, rt = 0;
+#pragma unroll
+            for (int i = 0; i < NC; ++i) {
+                const E *m0 = M0 + i * CM, *m1 = M1 + i * CM, *m2 = M2 + i * CM;
+                const E dE = m1[cm + 1] - m1[cm - 1];
+                const E dN = m2[cm] - m0[cm];
+                const E dNE = m2[cm + 1] - m0[cm - 1];
+                const E dSE = m0[cm + 1] - m2[cm - 1];
+                const E gx = (E)3 * fma((E)(1.0 / 9.0), dE, (E)(1.0 / 36.0) * (dNE + dSE));
+                const E gy = (E)3 * fma((E)(1.0 / 9.0), dN, (E)(1.0 / 36.0) * (dNE - dSE));
+                const E ri = (E)R1[i * CW + cc] + (E)L1[i * CW + cc];
+                rt += ri;
+                const E rmi = ri * V::invM(P, i);
+                const E fx = -rmi * gx, fy = -rmi * gy;
+                Fsx += fx;
+                Fsy += fy;
+                Fx[i] = (float)fx;
+                Fy[i] = (float)fy;
+            }
+            const E irt = (E)1 / rt;
+            const float ux = (float)(fma((E)0.5, Fsx, (E)jx) * irt);
+            const float uy = (float)(fma((E)0.5, Fsy, (E)jy) * irt);
+            const float u2 = ux * ux + uy * uy;
+            float ue[9], Bq[9], c9[9];
+#pragma unroll
+            for (int a = 0; a < 9; ++a) {
+                ue[a] = (float)L::e(a, 0) * ux + (float)L::e(a, 1) * uy;
+                Bq[a] = ue[a] * fmaf(4.5f, ue[a], 3.0f) - 1.5f * u2;
+                c9[a] = fmaf(9.0f, ue[a], 3.0f);
+            }
+#pragma unroll
+            for (int i = 0; i < NC; ++i) {
+                const float *r0 = R0 + i * CW, *r1 = R1 + i * CW, *r2 = R2 + i * CW;
+                const float dE = r1[cc + 1] - r1[cc - 1];
+                const float dN = r2[cc] - r0[cc];
+                const float dNE = r2[cc + 1] - r0[cc - 1];
+                const float dSE = r0[cc + 1] - r2[cc - 1];
+                const float Gx = 3.0f * fmaf(1.0f / 9.0f, dE, (1.0f / 36.0f) * (dNE + dSE));
+                const float Gy = 3.0f * fmaf(1.0f / 9.0f, dN, (1.0f / 36.0f) * (dNE - dSE));
+                const float ri = r1[cc] + L1[i * CW + cc];
+                const float Fu3 = 3.0f * (Fx[i] * ux + Fy[i] * uy);
+                const float Gu = Gx * ux + Gy * uy;
+                float os = 0.0f, oc = 0.0f;
+#pragma unroll
+                for (int a = 1; a < 9; ++a) {
+                    const int ex = L::e(a, 0), ey = L::e(a, 1);
+                    const float wa = (float)L::w(a);
+                    const float va = kKeep ? hv[kKeep ? i : 0][a - 1] : __ldg(gin + (i * 8 + a - 1) * N + rc);
+                    const float Fe = (float)ex * Fx[i] + (float)ey * Fy[i];
+                    const float Ge = (float)ex * Gx + (float)ey * Gy;
+                    const float cW = (float)(0.5 * (3.0 * (ex * ex + ey * ey) - 2.0) - 1.0);
+                    // Eq. (1c) forcing, Eq. (1b) equilibrium, Eq. (1a) BGK
+                    const float Fa = wa * (fmaf(Fe, c9[a], -Fu3) + fmaf(3.0f * ue[a], Ge, cW * Gu));
+                    const float gs = fmaf(om, wa * ri * Bq[a] - va, va) + cF * Fa;
+                    if (interior && own_row) gout[(i * 8 + a - 1) * N + yd[ey + 1] + xd[ex + 1]] = gs;
+                    acc_add(os, oc, gs);
+                    if (ex == 0)
+                        ownv[ey + 1][i] = gs;
+                    else
+                        XC[(((ey + 1) * 2 + (ex > 0 ? 0 : 1)) * NC + i) * kT + t] = gs;
+                }
+                oS[i] = os;
+                oC[i] = oc;
+            }
+        }
+        __syncthreads();
+        // ---- density update of the interior columns ---------------------------------
+        if (interior) {
+            const bool write_row = (crow - 1) >= y0 && (crow - 1) < y0 + h;
+            const long long rw = (long long)wrapc(crow - 1, ny) * nx + xg;
+            const int cc = col + 3;
+            const float *Rh = RS + ((q + 3) & 3) * NC * CW;  // row crow-1
+            const float *Rl = RL + ((q + 3) & 3) * NC * CW;
+#pragma unroll
+            for (int i = 0; i < NC; ++i) {
+                const float *x0p = XC + ((0 * 2 + 0) * NC + i) * kT, *x0m = XC + ((0 * 2 + 1) * NC + i) * kT;
+                const float *x1p = XC + ((1 * 2 + 0) * NC + i) * kT, *x1m = XC + ((1 * 2 + 1) * NC + i) * kT;
+                const float *x2p = XC + ((2 * 2 + 0) * NC + i) * kT, *x2m = XC + ((2 * 2 + 1) * NC + i) * kT;
+                // arrivals into row crow-1: completes that row
+                acc_add(aS[i], aC[i], x0p[t - 1]);
+                acc_add(aS[i], aC[i], ownv[0][i]);
+                acc_add(aS[i], aC[i], x0m[t + 1]);
+                if (write_row) {
+                    float hi = Rh[i * CW + cc], lo = Rl[i * CW + cc];
+                    pair_add(hi, lo, aS[i], aC[i]);
+                    out.rhi_f()[i * N + rw] = hi;
+                    out.rlo[i * N + rw] = lo;
+                    acc_add(msum[i], mcmp[i], hi);
+                    mcmp[i] += lo;
+                }
+                // row crow: departures of this node, arrivals from the same row
+                aS[i] = bS[i];
+                aC[i] = bC[i];
+                acc_add(aS[i], aC[i], -oS[i]);
+                aC[i] -= oC[i];
+                acc_add(aS[i], aC[i], x1p[t - 1]);
+                acc_add(aS[i], aC[i], x1m[t + 1]);
+                // row crow+1: first arrivals
+                bS[i] = 0.0f;
+                bC[i] = 0.0f;
+                acc_add(bS[i], bC[i], x2p[t - 1]);
+                acc_add(bS[i], bC[i], ownv[2][i]);
+                acc_add(bS[i], bC[i], x2m[t + 1]);
+            }
+        }
+    }
+    if (mass_partials) {
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+            double v = (double)msum[i] + (double)mcmp[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if ((t & 31) == 0) RED[(t >> 5) * NC + i] = v;
+        }
+        __syncthreads();
+        if (t < NC) {
+            double s = 0.0;
+            for (int wv = 0; wv < kT / 32; ++wv) s += RED[wv * NC + t];
+            mass_partials[((long long)blockIdx.y * gridDim.x + blockIdx.x) * NC + t] = s;
+        }
+    }
+}
+
+// R(0) = sum_a g_{a,i} for every node (fixed order a = 0..8).
+template <int NC, typename S>
+__global__ void k_density(const Params P, const S *__restrict__ g, S *__restrict__ R)
+{
+    const long long N = P.N;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N;
+         r += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+            S s = 0;
+#pragma unroll
+            for (int a = 0; a < 9; ++a) s += g[(i * 9 + a) * N + r];
+            R[i * N + r] = s;
+        }
+    }
+}
+
+struct Ops {
+    int (*density)(const Params &, StateBufs, cudaStream_t);
+    int (*step)(const Params &, const FusedGeom &, StateBufs, StateBufs, double *, cudaStream_t);
+    size_t (*smem)(int W);
+    int (*occupancy)(size_t smem);
+};
+
+// S = double: binary64 kernel (all populations, binary64 densities).
+// S = float:  binary32 kernel with thermodynamics in E.
+template <int NC, typename S, typename E> struct Impl {
+    static constexpr bool k64 = sizeof(S) == 8;
+    static auto kernel()
+    {
+        if constexpr (k64) return k_fused<NC, double, double>;
+        else return k_fused32<NC, E>;
+    }
+    static int density(const Params &P, StateBufs st, cudaStream_t s)
+    {
+        if constexpr (k64) {
+            long long b = (P.N + 255) / 256;
+            if (b > 152 * 32) b = 152 * 32;
+            k_density<NC, double><<<(unsigned)b, 256, 0, s>>>(P, (const double *)st.g, st.rhi_d());
+        }
+        return (int)cudaGetLastError();
+    }
+    static size_t smem(int W)
+    {
+        if constexpr (k64) return Smem<NC, double, double>::total(W);
+        else return Smem32<NC, E>::total(W);
+    }
+    static int occupancy(size_t bytes)
+    {
+        // the limit is the widest strip's need, so that problems of other
+        // widths launched later keep fitting under it
+        if (cudaFuncSetAttribute(kernel(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem(kWmax)) != cudaSuccess)
+            return 0;
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel(), kT, bytes) != cudaSuccess)
+            return 0;
+        return n;
+    }
+    static int step(const Params &P, const FusedGeom &g, StateBufs in, StateBufs out, double *mp,
+                    cudaStream_t s)
+    {
+        dim3 grid(g.nstrips, g.segs);
+        if constexpr (k64)
+            k_fused<NC, double, double><<<grid, kT, g.smem, s>>>(
+                P, g.strip, g.seg_h, (const double *)in.g, (double *)out.g, in.rhi_d(),
+                out.rhi_d(), mp);
+        else
+            k_fused32<NC, E><<<grid, kT, g.smem, s>>>(P, g.strip, g.seg_h, in, out, mp);
+        return (int)cudaGetLastError();
+    }
+};
+
+template <int NC, typename S, typename E> const Ops *ops_of()
+{
+    static const Ops o = {&Impl<NC, S, E>::density, &Impl<NC, S, E>::step, &Impl<NC, S, E>::smem,
+                          &Impl<NC, S, E>::occupancy};
+    return &o;
+}
+
+template <typename S, typename E, int LO, int HI> const Ops *ops_range(int nc)
+{
+    if constexpr (LO > HI) {
+        return nullptr;
+    } else {
+        if (nc == LO) return ops_of<LO, S, E>();
+        return ops_range<S, E, LO + 1, HI>(nc);
+    }
+}
+
+}  // namespace fz
+}  // namespace lbmfug
+
+#define LBM_FZ_TU(NAME, S, E, LO, HI)                                                          \
+    namespace lbmfug {                                                                         \
+    namespace fz {                                                                             \
+    const Ops *NAME(int nc) { return ops_range<S, E, LO, HI>(nc); }                            \
+    }                                                                                          \
+    }

@@ -8,13 +8,28 @@
 
 namespace lbmfug {
 
-// Scratch fields of the three-pass schedule (device, binary64).
+// Device state of one time level.
+//  binary64 storage: g = all Q populations [nc][Q][N] (double); the fused
+//    schedule also keeps the densities rhi = [nc][N] (double).
+//  binary32 storage: g = the Q-1 moving populations [nc][Q-1][N] (float) and
+//    the densities as the pair rhi + rlo ([nc][N] float each).
+struct StateBufs {
+    void *g = nullptr;
+    void *rhi = nullptr;
+    float *rlo = nullptr;
+    __host__ __device__ float *rhi_f() const { return (float *)rhi; }
+    __host__ __device__ double *rhi_d() const { return (double *)rhi; }
+};
+
+// Scratch fields of the three-pass schedule (device).
 struct ThreePassWork {
     double *rho;  // [nc][N] mass densities rho_i
     double *lnf;  // [nc][N] ln f_i
     double *psi;  // [N]     psi = sum_j sqrt(kappa_j) rho~_j
     double *lap;  // [N]     lap psi
     double *jm;   // [D][N]  sum_i sum_a e_a g_{a,i}
+    float *osum;  // [nc][N] binary32 storage: compensated sum of the populations
+    float *ocmp;  //         that left each node in the last collision
 };
 
 // Fused single-pass D2Q9 schedule: density state and launch geometry.
@@ -28,29 +43,32 @@ struct FusedGeom {
 };
 
 // All launchers return a cudaError_t cast to int (0 = success).
-// prec: 0 = binary64 storage, 1 = binary32 deviation storage.
+// Three-pass prec: 0 = binary64 storage, 1 = binary32 deviation storage
+// (thermodynamics in binary64).  Fused prec: 0 = binary64, 1 = binary32
+// deviation storage with binary64 thermodynamics, 2 = binary32 throughout.
 int launch_init_equilibrium(int lat, int prec, int nc, const Params &P, const double *rho,
-                            const double *u, void *g, cudaStream_t s);
-int launch_threepass_step(int lat, int prec, int nc, const Params &P, const void *gin, void *gout,
+                            const double *u, StateBufs st, cudaStream_t s);
+int launch_threepass_step(int lat, int prec, int nc, const Params &P, StateBufs in, StateBufs out,
                           const ThreePassWork &w, cudaStream_t s);
-// Macroscopic outputs of state g into device buffers (any may be null).
-int launch_fields(int lat, int prec, int nc, const Params &P, const void *g,
+int threepass_launches_per_step(int lat, int prec, int nc);
+// Macroscopic outputs of state st into device buffers (any may be null).
+int launch_fields(int lat, int prec, int nc, const Params &P, StateBufs st,
                   const ThreePassWork &w, double *rho, double *u, double *p, double *lnf,
                   cudaStream_t s);
-// Populations <-> binary64 post-streaming layout.
-int launch_state_to_f64(int lat, int prec, int nc, const Params &P, const void *g, double *out,
+// Populations <-> binary64 post-streaming layout [nc][Q][N].
+int launch_state_to_f64(int lat, int prec, int nc, const Params &P, StateBufs st, double *out,
                         cudaStream_t s);
-int launch_state_from_f64(int lat, int prec, int nc, const Params &P, const double *in, void *g,
-                          cudaStream_t s);
+int launch_state_from_f64(int lat, int prec, int nc, const Params &P, const double *in,
+                          StateBufs st, cudaStream_t s);
 
-// Fused D2Q9 schedule (lbm_fused2d.cu).
-bool fused_supported(int lat, int nc);
+// Fused D2Q9 schedule (lbm_fused2d.cu).  prec as the options: 0 binary64,
+// 1 binary32 storage with binary64 thermodynamics, 2 binary32 throughout.
+bool fused_supported(int lat, int prec, int nc);
 FusedGeom fused_geometry(int prec, int nc, const Params &P, int num_sms);
-int launch_fused_density(int prec, int nc, const Params &P, const void *g, void *rho_state,
-                         cudaStream_t s);
-int launch_fused_step(int prec, int nc, const Params &P, const FusedGeom &geo, const void *gin,
-                      void *gout, const void *rho_in, void *rho_out, double *mass_partials,
-                      cudaStream_t s);
+// binary64 only: densities of the fused state from the populations
+int launch_fused_density(int prec, int nc, const Params &P, StateBufs st, cudaStream_t s);
+int launch_fused_step(int prec, int nc, const Params &P, const FusedGeom &geo, StateBufs in,
+                      StateBufs out, double *mass_partials, cudaStream_t s);
 // Sum the per-CTA mass partials of a monitored fused step into out[nc].
 int launch_fused_mass_final(int nc, const FusedGeom &geo, const double *partials, double *out,
                             int *nonfinite, cudaStream_t s);

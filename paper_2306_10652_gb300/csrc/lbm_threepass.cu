@@ -31,39 +31,45 @@ constexpr int kBad = (int)cudaErrorInvalidValue;
 }  // namespace
 
 int launch_init_equilibrium(int lat, int prec, int nc, const Params &P, const double *rho,
-                            const double *u, void *g, cudaStream_t s)
+                            const double *u, StateBufs st, cudaStream_t s)
 {
     const tp::Ops *o = lookup(lat, prec, nc);
-    return o ? o->init(P, rho, u, g, s) : kBad;
+    return o ? o->init(P, rho, u, st, s) : kBad;
 }
 
-int launch_threepass_step(int lat, int prec, int nc, const Params &P, const void *gin, void *gout,
+int launch_threepass_step(int lat, int prec, int nc, const Params &P, StateBufs in, StateBufs out,
                           const ThreePassWork &w, cudaStream_t s)
 {
     const tp::Ops *o = lookup(lat, prec, nc);
-    return o ? o->step(P, gin, gout, w, s) : kBad;
+    return o ? o->step(P, in, out, w, s) : kBad;
 }
 
-int launch_fields(int lat, int prec, int nc, const Params &P, const void *g,
+int threepass_launches_per_step(int lat, int prec, int nc)
+{
+    const tp::Ops *o = lookup(lat, prec, nc);
+    return o ? o->launches_per_step() : 0;
+}
+
+int launch_fields(int lat, int prec, int nc, const Params &P, StateBufs st,
                   const ThreePassWork &w, double *rho, double *u, double *p, double *lnf,
                   cudaStream_t s)
 {
     const tp::Ops *o = lookup(lat, prec, nc);
-    return o ? o->fields(P, g, w, rho, u, p, lnf, s) : kBad;
+    return o ? o->fields(P, st, w, rho, u, p, lnf, s) : kBad;
 }
 
-int launch_state_to_f64(int lat, int prec, int nc, const Params &P, const void *g, double *out,
+int launch_state_to_f64(int lat, int prec, int nc, const Params &P, StateBufs st, double *out,
                         cudaStream_t s)
 {
     const tp::Ops *o = lookup(lat, prec, nc);
-    return o ? o->to_f64(P, g, out, s) : kBad;
+    return o ? o->to_f64(P, st, out, s) : kBad;
 }
 
-int launch_state_from_f64(int lat, int prec, int nc, const Params &P, const double *in, void *g,
-                          cudaStream_t s)
+int launch_state_from_f64(int lat, int prec, int nc, const Params &P, const double *in,
+                          StateBufs st, cudaStream_t s)
 {
     const tp::Ops *o = lookup(lat, prec, nc);
-    return o ? o->from_f64(P, in, g, s) : kBad;
+    return o ? o->from_f64(P, in, st, s) : kBad;
 }
 
 }  // namespace lbmfug

@@ -23,7 +23,7 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 LBM_D2Q9, LBM_D3Q19 = 0, 1
-LBM_FP64, LBM_FP32DEV = 0, 1
+LBM_FP64, LBM_FP32DEV, LBM_FP32 = 0, 1, 2
 LBM_SCHED_AUTO, LBM_SCHED_THREEPASS, LBM_SCHED_FUSED = 0, 1, 2
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENONFINITE, LBM_ETIMEOUT, LBM_ESTATE, LBM_ENOTSUP = \
     0, -1, -2, -3, -4, -5, -6, -7

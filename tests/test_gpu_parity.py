@@ -20,7 +20,7 @@ from paper_2306_10652_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-FP64, FP32DEV = 0, 1
+FP64, FP32DEV, FP32 = 0, 1, 2
 THREEPASS, AUTO, FUSED = 1, 0, 2
 
 
@@ -76,6 +76,13 @@ def test_one_step_fp32dev(case, schedule):
     assert one_step_case(seed, nc, lattice, shape, tau, Mr, FP32DEV, schedule) < 2e-6
 
 
+@pytest.mark.parametrize("case", CASES[:6], ids=lambda c: f"lat{c[2]}-nc{c[1]}")
+def test_one_step_fp32(case):
+    """Binary32 thermodynamics (fused schedule): one step within 1e-5 of max |g_i|."""
+    seed, nc, lattice, shape, tau, Mr = case
+    assert one_step_case(seed, nc, lattice, shape, tau, Mr, FP32, AUTO) < 1e-5
+
+
 def test_ten_steps_fp64_two_phase():
     # liquid-range densities inside the two-phase region: strong forces
     assert one_step_case(11, 3, 0, (1, 24, 40), nsteps=10, lo=0.05, hi=0.6) < 1e-11
@@ -108,28 +115,28 @@ def test_flat_interface_1000_steps_fp64(schedule):
     assert np.abs(m["p"] - ref["p"]).max() <= 1e-9
 
 
-@pytest.mark.parametrize("schedule", [THREEPASS, AUTO])
-def test_fp32dev_mass_and_equilibrium(schedule):
+@pytest.mark.parametrize("schedule,prec32", [(THREEPASS, FP32DEV), (AUTO, FP32DEV), (AUTO, FP32)])
+def test_fp32dev_mass_and_equilibrium(schedule, prec32):
     """Binary32 deviation storage against the binary64 path: per-component
     mass within 1e-6 relative, and the converged phase mole fractions (phase
     centres, same sublattice) within 1e-5."""
     c, orc, rho = flat_interface_case(nx=64, ny=2)
     m0 = orc.mass(orc.init_equilibrium(rho))
     res = {}
-    for prec in (FP64, FP32DEV):
+    for prec in (FP64, prec32):
         with gpu_problem(c, 0, orc.shape, precision=prec, schedule=schedule) as gp:
             gp.init_fields(rho)
             gp.step(1000)
             mass = gp.mass()
-            if prec == FP32DEV:
+            if prec != FP64:
                 assert np.abs(mass / m0 - 1).max() <= 1e-6
             gp.step(39000)
             r = gp.moments(("rho",))["rho"][:, 0, 0]
             res[prec] = (r[:, 32] / r[:, 32].sum(), r[:, 0] / r[:, 0].sum())
-            if prec == FP32DEV:
+            if prec != FP64:
                 assert np.abs(gp.mass() / m0 - 1).max() <= 1e-6
     for k in range(2):
-        assert np.abs(res[FP32DEV][k] - res[FP64][k]).max() <= 1e-5, (res[FP32DEV][k], res[FP64][k])
+        assert np.abs(res[prec32][k] - res[FP64][k]).max() <= 1e-5, (res[prec32][k], res[FP64][k])
 
 
 @pytest.mark.parametrize("lattice,shape,nc", [(0, (1, 12, 17), 3), (1, (4, 5, 6), 2)])
@@ -152,7 +159,8 @@ def test_moments_match_oracle(lattice, shape, nc):
         assert np.abs(m[k] - ref[k]).max() <= 1e-13 * scale + 1e-15, k
 
 
-@pytest.mark.parametrize("precision,schedule", [(FP64, THREEPASS), (FP64, AUTO), (FP32DEV, AUTO)])
+@pytest.mark.parametrize("precision,schedule", [(FP64, THREEPASS), (FP64, AUTO), (FP32DEV, AUTO),
+                                                (FP32, AUTO)])
 def test_mass_conservation_and_uniform_fixed_point(precision, schedule):
     shape = (1, 40, 70)
     c = seeded_mixture(31, 3, 0, shape)
@@ -217,3 +225,34 @@ def test_zero_steps_and_step_count():
         assert np.array_equal(gp.get_state(), g0)
         gp.step(3)
         assert gp.step_count() == 3
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32DEV])
+def test_monitor_matches_mass(precision):
+    """The fused per-step mass monitor equals the separate reduction."""
+    shape = (1, 37, 300)
+    c = seeded_mixture(71, 3, 0, shape)
+    rho = smooth_rho(71, c, shape)
+    with gpu_problem(c, 0, shape, precision=precision, monitor_every=5) as gp:
+        gp.init_fields(rho)
+        gp.step(10)
+        m, at, nf = gp.monitor()
+        assert at == 10 and not nf
+        ref = gp.mass()
+        assert np.allclose(m, ref, rtol=1e-12 if precision == FP64 else 1e-6, atol=0)
+
+
+def test_fused_matches_threepass_many_shapes():
+    """Fused and three-pass schedules agree step by step (binary64) on shapes
+    that exercise ragged strips and segments and periodic wrap."""
+    for k, shape in enumerate([(1, 3, 300), (1, 130, 127), (1, 2, 253), (1, 64, 5), (1, 1, 1)]):
+        c = seeded_mixture(80 + k, 2, 0, shape)
+        rho = smooth_rho(80 + k, c, shape)
+        out = []
+        for sched in (THREEPASS, FUSED):
+            with gpu_problem(c, 0, shape, precision=FP64, schedule=sched) as gp:
+                gp.init_fields(rho, synth.random_velocity(k, 2, shape, 1e-3))
+                gp.step(7)
+                out.append(gp.get_state())
+        scale = np.abs(out[0]).max()
+        assert np.abs(out[0] - out[1]).max() <= 1e-12 * scale, shape
