@@ -54,7 +54,7 @@ bool fused_supported(int lat, int prec, int nc)
 {
     if (lat != 0) return false;
     const fz::Ops *o = lookup(prec, nc);
-    return o && o->smem(fz::kWmax) <= max_optin_smem();
+    return o && o->smem(o->wmax) <= max_optin_smem();
 }
 
 FusedGeom fused_geometry(int prec, int nc, const Params &P, int num_sms)
@@ -63,8 +63,8 @@ FusedGeom fused_geometry(int prec, int nc, const Params &P, int num_sms)
     const fz::Ops *o = lookup(prec, nc);
     if (!o) return g;
     g.threads = fz::kT;
-    g.nstrips = (P.nx + fz::kWmax - 1) / fz::kWmax;
-    g.strip = (P.nx + g.nstrips - 1) / g.nstrips;   // balanced strip width <= kWmax
+    g.nstrips = (P.nx + o->wmax - 1) / o->wmax;
+    g.strip = (P.nx + g.nstrips - 1) / g.nstrips;   // balanced strip width <= wmax
     g.smem = o->smem(g.strip);
     int per_sm = o->occupancy(g.smem);
     if (per_sm < 1) per_sm = 1;

@@ -335,38 +335,50 @@ template <int NC, typename E> struct Smem32 {
     static __host__ __device__ constexpr size_t mu(int W) { return align16((size_t)3 * NC * (W + 4) * sizeof(E)); }
     static __host__ __device__ constexpr size_t xc() { return align16((size_t)6 * NC * kT * sizeof(float)); }
     static __host__ __device__ constexpr size_t red() { return align16((size_t)(kT / 32) * NC * sizeof(double)); }
-    static __host__ __device__ constexpr size_t total(int W) { return 2 * rs(W) + ps(W) + mu(W) + xc() + red(); }
+    static __host__ __device__ constexpr size_t ms() { return align16((size_t)2 * NC * kT * sizeof(float)); }
+    static __host__ __device__ constexpr size_t total(int W) { return 2 * rs(W) + ps(W) + mu(W) + xc() + red() + ms(); }
 };
+constexpr int kWmax32 = kT - 6;  // binary32 kernel: one density column per thread
 
 // Binary32 state: the 8 moving populations g[i][a-1][node] (a = 1..8) and the
 // density rho_i = hi + lo.  Collision arithmetic in binary32; thermodynamics
 // and forces in E.  The new density of a node is its old density minus the
-// populations that left it plus those that arrived, all compensated sums of
-// the stored binary32 values, so the component mass is conserved to the
-// rounding of the pair.
-template <int NC, typename E>
+// populations that left it plus those that arrived: every stored binary32
+// population is added once where it arrives and subtracted once where it
+// left, each by an error-free Fast2Sum into the (hi, lo) pair of the node,
+// so the component mass is conserved to the rounding of the pairs.
+// Fast2Sum is exact when |hi| >= |term|, i.e. when no single moving
+// population exceeds the density of the node it leaves or enters.
+__device__ __forceinline__ void pair_acc(float &hi, float &lo, float x)
+{
+    const float s = hi + x;
+    lo += x - (s - hi);
+    hi = s;
+}
+
+template <int NC, typename E, typename IDX>
 __global__ void __launch_bounds__(kT)
     k_fused32(const Params P, const int W, const int H, StateBufs in, StateBufs out,
               double *__restrict__ mass_partials)
 {
     using L = Lattice<0>;
     using V = PV<E>;
-    constexpr bool kKeep = 8 * NC * sizeof(float) <= 352;  // moving populations held in registers
-    extern __shared__ __align__(16) unsigned char smem[];
     using SM = Smem32<NC, E>;
-    float *RS = (float *)smem;                                 // [4][NC][W+6] rho hi rows
-    float *RL = (float *)(smem + SM::rs(W));                   // [4][NC][W+6] rho lo rows
-    E *PS = (E *)(smem + 2 * SM::rs(W));                       // [3][W+6]     psi rows
-    E *MU = (E *)(smem + 2 * SM::rs(W) + SM::ps(W));           // [3][NC][W+4] mu rows
-    float *XC = (float *)(smem + 2 * SM::rs(W) + SM::ps(W) + SM::mu(W));  // [6][NC][kT]
-    double *RED = (double *)(smem + 2 * SM::rs(W) + SM::ps(W) + SM::mu(W) + SM::xc());
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *RS = (float *)smem;                                   // [4][NC][W+6] rho hi rows
+    float *RL = (float *)(smem + SM::rs(W));                     // [4][NC][W+6] rho lo rows
+    E *PS = (E *)(smem + 2 * SM::rs(W));                         // [3][W+6]     psi rows
+    E *MU = (E *)(smem + 2 * SM::rs(W) + SM::ps(W));             // [3][NC][W+4] mu rows
+    float *XC = (float *)(smem + 2 * SM::rs(W) + SM::ps(W) + SM::mu(W));  // [6][NC][kT] exchange
+    double *RED = (double *)((unsigned char *)XC + SM::xc());
+    float *MS = (float *)((unsigned char *)RED + SM::red());     // [2][NC][kT] mass of rows written
     const float *gin = (const float *)in.g;
     float *gout = (float *)out.g;
     const float *rhin = in.rhi_f();
     const float *rlin = in.rlo;
 
     const int nx = P.nx, ny = P.ny;
-    const long long N = P.N;
+    const IDX N = (IDX)P.N;
     const int CW = W + 6, CM = W + 4;
     const int x0 = blockIdx.x * W;
     const int w = min(W, nx - x0);
@@ -378,28 +390,28 @@ __global__ void __launch_bounds__(kT)
     const bool interior = col >= 0 && col < w;
     const int xg = wrapc(x0 + col, nx);
     const int xd[3] = {wrapc(xg - 1, nx), xg, wrapc(xg + 1, nx)};
-    const int cA0 = t - 3, cA1 = t - 3 + kT;
-    const bool hasA0 = cA0 < w + 3, hasA1 = cA1 < w + 3;
-    const int xA0 = wrapc(x0 + cA0, nx), xA1 = hasA1 ? wrapc(x0 + cA1, nx) : 0;
+    // phase (A): one density column per thread (strips are at most kT - 6 wide)
+    const int cA0 = t - 3;
+    const bool hasA0 = cA0 < w + 3;
+    const int xA0 = wrapc(x0 + cA0, nx);
     const E RT = V::RT(P);
-    const float om = (float)P.omega, cF = (float)(1.0 - 0.5 * P.omega);
+    const float om = (float)P.omega, om1 = (float)(1.0 - P.omega), cF = (float)(1.0 - 0.5 * P.omega);
 
-    float msum[NC], mcmp[NC];     // mass of the rows written (compensated)
-    float aS[NC], aC[NC], bS[NC], bC[NC];  // pending density updates of rows crow-1, crow
-    float rh0[NC], rh1[NC], rl0[NC], rl1[NC];  // prefetched density pair of the next row
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
-        msum[i] = mcmp[i] = 0.0f;
-        aS[i] = aC[i] = bS[i] = bC[i] = 0.0f;
+        MS[(0 * NC + i) * kT + t] = 0.0f;
+        MS[(1 * NC + i) * kT + t] = 0.0f;
     }
+    float aH[NC], aL[NC], bH[NC], bL[NC];  // density pairs being updated: rows crow-1, crow
+    float rh0[NC], rl0[NC];                // prefetched density pair of the next row
+#pragma unroll
+    for (int i = 0; i < NC; ++i) aH[i] = aL[i] = bH[i] = bL[i] = 0.0f;
     {
-        const long long rowb = (long long)wrapc(y0 - 3, ny) * nx;
+        const IDX rowb = (IDX)wrapc(y0 - 3, ny) * (IDX)nx;
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
             rh0[i] = hasA0 ? __ldg(rhin + i * N + rowb + xA0) : 0.0f;
             rl0[i] = hasA0 ? __ldg(rlin + i * N + rowb + xA0) : 0.0f;
-            rh1[i] = hasA1 ? __ldg(rhin + i * N + rowb + xA1) : 0.0f;
-            rl1[i] = hasA1 ? __ldg(rlin + i * N + rowb + xA1) : 0.0f;
         }
     }
 
@@ -407,15 +419,6 @@ __global__ void __launch_bounds__(kT)
     for (int kk = 0; kk < nrows; ++kk) {
         const int k = y0 - 3 + kk;
         const int crow = k - 2;
-        const int yc = wrapc(crow, ny);
-        const long long rc = (long long)yc * nx + xg;
-        float hv[kKeep ? NC : 1][8];
-        if (kKeep && kk >= 4 && active) {
-#pragma unroll
-            for (int i = 0; i < NC; ++i)
-#pragma unroll
-                for (int a = 0; a < 8; ++a) hv[kKeep ? i : 0][a] = __ldg(gin + (i * 8 + a) * N + rc);
-        }
         // ---- (A) density pair and psi of row k ----------------------------------
         {
             const int s4 = kk & 3, s3 = kk % 3;
@@ -428,16 +431,6 @@ __global__ void __launch_bounds__(kT)
                     ps = fma(V::sqk(P, i), ((E)rh0[i] + (E)rl0[i]) * V::invM(P, i), ps);
                 }
                 PS[s3 * CW + cA0 + 3] = ps;
-            }
-            if (hasA1) {
-                E ps = 0;
-#pragma unroll
-                for (int i = 0; i < NC; ++i) {
-                    RS[(s4 * NC + i) * CW + cA1 + 3] = rh1[i];
-                    RL[(s4 * NC + i) * CW + cA1 + 3] = rl1[i];
-                    ps = fma(V::sqk(P, i), ((E)rh1[i] + (E)rl1[i]) * V::invM(P, i), ps);
-                }
-                PS[s3 * CW + cA1 + 3] = ps;
             }
         }
         __syncthreads();
@@ -452,8 +445,9 @@ __global__ void __launch_bounds__(kT)
                 const int cc = c + 3;
                 E rm[NC], lf[NC];
 #pragma unroll
-                for (int i = 0; i < NC; ++i)
+                for (int i = 0; i < NC; ++i) {
                     rm[i] = ((E)RS[(s4 * NC + i) * CW + cc] + (E)RL[(s4 * NC + i) * CW + cc]) * V::invM(P, i);
+                }
                 pr_lnf<NC, E>(P, rm, lf, nullptr);
                 const E c0 = p1[cc];
                 const E faces = (p1[cc + 1] - c0) + (p1[cc - 1] - c0) + (p2[cc] - c0) + (p0[cc] - c0);
@@ -464,50 +458,51 @@ __global__ void __launch_bounds__(kT)
                     MU[((q % 3) * NC + i) * CM + c + 2] = fma(RT, lf[i], -V::sqk(P, i) * lap);
             }
         }
-        __syncthreads();
         if (kk + 1 < nrows) {
-            const long long rowb = (long long)wrapc(k + 1, ny) * nx;
+            const IDX rowb = (IDX)wrapc(k + 1, ny) * (IDX)nx;
 #pragma unroll
             for (int i = 0; i < NC; ++i) {
                 if (hasA0) {
                     rh0[i] = __ldg(rhin + i * N + rowb + xA0);
                     rl0[i] = __ldg(rlin + i * N + rowb + xA0);
                 }
-                if (hasA1) {
-                    rh1[i] = __ldg(rhin + i * N + rowb + xA1);
-                    rl1[i] = __ldg(rlin + i * N + rowb + xA1);
-                }
             }
         }
+        __syncthreads();
         if (kk < 4) continue;
         // ---- (C) collision of row k-2 (moving populations only) --------------------
         const int q = kk - 2;
         const bool own_row = crow >= y0 && crow < y0 + h;
-        float ownv[3][NC];   // dx = 0 moving values by dy = -1, +1 (index 0, 2)
-        float oS[NC], oC[NC];  // what leaves this node
+        const int yc = wrapc(crow, ny);
+        float own0[NC], own2[NC];  // dx = 0 moving values, dy = -1 and +1
+        float dep[NC];             // sum of this node's departures
         if (active) {
-            const long long yd[3] = {(long long)wrapc(yc - 1, ny) * nx, (long long)yc * nx,
-                                     (long long)wrapc(yc + 1, ny) * nx};
+            const IDX yd[3] = {(IDX)wrapc(yc - 1, ny) * (IDX)nx, (IDX)yc * (IDX)nx,
+                               (IDX)wrapc(yc + 1, ny) * (IDX)nx};
+            IDX dst[9];
+#pragma unroll
+            for (int a = 1; a < 9; ++a) dst[a] = yd[L::e(a, 1) + 1] + (IDX)xd[L::e(a, 0) + 1];
             const int cc = col + 3, cm = col + 2;
             const float *R0 = RS + ((q + 3) & 3) * NC * CW;
             const float *R1 = RS + (q & 3) * NC * CW;
             const float *R2 = RS + ((q + 1) & 3) * NC * CW;
-            const float *L1 = RL + (q & 3) * NC * CW;
             const E *M0 = MU + ((q + 2) % 3) * NC * CM;
             const E *M1 = MU + (q % 3) * NC * CM;
             const E *M2 = MU + ((q + 1) % 3) * NC * CM;
+            const IDX rc = (IDX)yc * (IDX)nx + (IDX)xg;
+            float hv[NC][8];
+#pragma unroll
+            for (int i = 0; i < NC; ++i)
+#pragma unroll
+                for (int a = 0; a < 8; ++a) hv[i][a] = __ldg(gin + (i * 8 + a) * N + rc);
             float jx = 0.0f, jy = 0.0f;
 #pragma unroll
             for (int i = 0; i < NC; ++i) {
-                float v[9];
-                v[0] = 0.0f;
-#pragma unroll
-                for (int a = 1; a < 9; ++a)
-                    v[a] = kKeep ? hv[kKeep ? i : 0][a - 1] : __ldg(gin + (i * 8 + a - 1) * N + rc);
+                const float *v = hv[i] - 1;  // v[a], a = 1..8
                 jx += (v[1] - v[2]) + (v[5] - v[6]) + (v[7] - v[8]);
                 jy += (v[3] - v[4]) + (v[5] - v[6]) + (v[8] - v[7]);
             }
-            float Fx[NC], Fy[NC];
+            float Fx[NC], Fy[NC], rlo1[NC];
             E Fsx = 0, Fsy = 0, rt = 0;
 #pragma unroll
             for (int i = 0; i < NC; ++i) {
@@ -518,7 +513,8 @@ __global__ void __launch_bounds__(kT)
                 const E dSE = m0[cm + 1] - m2[cm - 1];
                 const E gx = (E)3 * fma((E)(1.0 / 9.0), dE, (E)(1.0 / 36.0) * (dNE + dSE));
                 const E gy = (E)3 * fma((E)(1.0 / 9.0), dN, (E)(1.0 / 36.0) * (dNE - dSE));
-                const E ri = (E)R1[i * CW + cc] + (E)L1[i * CW + cc];
+                rlo1[i] = RL[((q & 3) * NC + i) * CW + cc];
+                const E ri = (E)R1[i * CW + cc] + (E)rlo1[i];
                 rt += ri;
                 const E rmi = ri * V::invM(P, i);
                 const E fx = -rmi * gx, fy = -rmi * gy;
@@ -531,12 +527,15 @@ __global__ void __launch_bounds__(kT)
             const float ux = (float)(fma((E)0.5, Fsx, (E)jx) * irt);
             const float uy = (float)(fma((E)0.5, Fsy, (E)jy) * irt);
             const float u2 = ux * ux + uy * uy;
-            float ue[9], Bq[9], c9[9];
+            // per-direction constants of Eqs. (1a)-(1c):
+            //   g* = (1-w) g + rho (w w_a B_a) + cF w_a [Fe (3 + 9 ue) + 3 ue Ge + K_class]
+            float WB[9], C9[9], U3[9];
 #pragma unroll
-            for (int a = 0; a < 9; ++a) {
-                ue[a] = (float)L::e(a, 0) * ux + (float)L::e(a, 1) * uy;
-                Bq[a] = ue[a] * fmaf(4.5f, ue[a], 3.0f) - 1.5f * u2;
-                c9[a] = fmaf(9.0f, ue[a], 3.0f);
+            for (int a = 1; a < 9; ++a) {
+                const float ue = (float)L::e(a, 0) * ux + (float)L::e(a, 1) * uy;
+                WB[a] = om * (float)L::w(a) * (ue * fmaf(4.5f, ue, 3.0f) - 1.5f * u2);
+                C9[a] = fmaf(9.0f, ue, 3.0f);
+                U3[a] = 3.0f * ue;
             }
 #pragma unroll
             for (int i = 0; i < NC; ++i) {
@@ -547,77 +546,76 @@ __global__ void __launch_bounds__(kT)
                 const float dSE = r0[cc + 1] - r2[cc - 1];
                 const float Gx = 3.0f * fmaf(1.0f / 9.0f, dE, (1.0f / 36.0f) * (dNE + dSE));
                 const float Gy = 3.0f * fmaf(1.0f / 9.0f, dN, (1.0f / 36.0f) * (dNE - dSE));
-                const float ri = r1[cc] + L1[i * CW + cc];
+                const float ri = r1[cc] + rlo1[i];
                 const float Fu3 = 3.0f * (Fx[i] * ux + Fy[i] * uy);
                 const float Gu = Gx * ux + Gy * uy;
-                float os = 0.0f, oc = 0.0f;
+                // cW = (3 e^2 - D)/2 - 1 with D = 2: faces -1/2, diagonals +1
+                const float Kf = fmaf(-0.5f, Gu, -Fu3), Kd = Gu - Fu3;
+                const float *v = hv[i] - 1;  // v[a], a = 1..8
+                float d = 0.0f;
 #pragma unroll
                 for (int a = 1; a < 9; ++a) {
                     const int ex = L::e(a, 0), ey = L::e(a, 1);
-                    const float wa = (float)L::w(a);
-                    const float va = kKeep ? hv[kKeep ? i : 0][a - 1] : __ldg(gin + (i * 8 + a - 1) * N + rc);
+                    const float cw = cF * (float)L::w(a);
                     const float Fe = (float)ex * Fx[i] + (float)ey * Fy[i];
                     const float Ge = (float)ex * Gx + (float)ey * Gy;
-                    const float cW = (float)(0.5 * (3.0 * (ex * ex + ey * ey) - 2.0) - 1.0);
-                    // Eq. (1c) forcing, Eq. (1b) equilibrium, Eq. (1a) BGK
-                    const float Fa = wa * (fmaf(Fe, c9[a], -Fu3) + fmaf(3.0f * ue[a], Ge, cW * Gu));
-                    const float gs = fmaf(om, wa * ri * Bq[a] - va, va) + cF * Fa;
-                    if (interior && own_row) gout[(i * 8 + a - 1) * N + yd[ey + 1] + xd[ex + 1]] = gs;
-                    acc_add(os, oc, gs);
-                    if (ex == 0)
-                        ownv[ey + 1][i] = gs;
-                    else
+                    const float Fa = fmaf(Fe, C9[a], fmaf(U3[a], Ge, (ex != 0 && ey != 0) ? Kd : Kf));
+                    const float gs = fmaf(om1, v[a], fmaf(ri, WB[a], cw * Fa));
+                    if (interior && own_row) gout[(i * 8 + a - 1) * N + dst[a]] = gs;
+                    d += gs;
+                    if (ex == 0) {
+                        if (ey < 0) own0[i] = gs;
+                        else own2[i] = gs;
+                    } else {
                         XC[(((ey + 1) * 2 + (ex > 0 ? 0 : 1)) * NC + i) * kT + t] = gs;
+                    }
                 }
-                oS[i] = os;
-                oC[i] = oc;
+                dep[i] = d;
             }
         }
         __syncthreads();
         // ---- density update of the interior columns ---------------------------------
         if (interior) {
             const bool write_row = (crow - 1) >= y0 && (crow - 1) < y0 + h;
-            const long long rw = (long long)wrapc(crow - 1, ny) * nx + xg;
+            const IDX rw = (IDX)wrapc(crow - 1, ny) * (IDX)nx + (IDX)xg;
             const int cc = col + 3;
-            const float *Rh = RS + ((q + 3) & 3) * NC * CW;  // row crow-1
-            const float *Rl = RL + ((q + 3) & 3) * NC * CW;
+            const float *Rh2 = RS + ((q + 1) & 3) * NC * CW;  // row crow+1
 #pragma unroll
             for (int i = 0; i < NC; ++i) {
-                const float *x0p = XC + ((0 * 2 + 0) * NC + i) * kT, *x0m = XC + ((0 * 2 + 1) * NC + i) * kT;
-                const float *x1p = XC + ((1 * 2 + 0) * NC + i) * kT, *x1m = XC + ((1 * 2 + 1) * NC + i) * kT;
-                const float *x2p = XC + ((2 * 2 + 0) * NC + i) * kT, *x2m = XC + ((2 * 2 + 1) * NC + i) * kT;
-                // arrivals into row crow-1: completes that row
-                acc_add(aS[i], aC[i], x0p[t - 1]);
-                acc_add(aS[i], aC[i], ownv[0][i]);
-                acc_add(aS[i], aC[i], x0m[t + 1]);
+                const float *xc = XC + i * kT;  // slot s of component i at xc[s * NC * kT]
+                // row crow-1: last arrivals complete its update
+                pair_acc(aH[i], aL[i], xc[0 * NC * kT + t - 1]);
+                pair_acc(aH[i], aL[i], own0[i]);
+                pair_acc(aH[i], aL[i], xc[1 * NC * kT + t + 1]);
                 if (write_row) {
-                    float hi = Rh[i * CW + cc], lo = Rl[i * CW + cc];
-                    pair_add(hi, lo, aS[i], aC[i]);
+                    const float hi = aH[i] + aL[i];
+                    const float lo = aL[i] - (hi - aH[i]);
                     out.rhi_f()[i * N + rw] = hi;
                     out.rlo[i * N + rw] = lo;
-                    acc_add(msum[i], mcmp[i], hi);
-                    mcmp[i] += lo;
+                    float ms = MS[(0 * NC + i) * kT + t], mc = MS[(1 * NC + i) * kT + t];
+                    acc_add(ms, mc, hi);
+                    MS[(0 * NC + i) * kT + t] = ms;
+                    MS[(1 * NC + i) * kT + t] = mc + lo;
                 }
-                // row crow: departures of this node, arrivals from the same row
-                aS[i] = bS[i];
-                aC[i] = bC[i];
-                acc_add(aS[i], aC[i], -oS[i]);
-                aC[i] -= oC[i];
-                acc_add(aS[i], aC[i], x1p[t - 1]);
-                acc_add(aS[i], aC[i], x1m[t + 1]);
-                // row crow+1: first arrivals
-                bS[i] = 0.0f;
-                bC[i] = 0.0f;
-                acc_add(bS[i], bC[i], x2p[t - 1]);
-                acc_add(bS[i], bC[i], ownv[2][i]);
-                acc_add(bS[i], bC[i], x2m[t + 1]);
+                // row crow: its departures, then arrivals along the row
+                aH[i] = bH[i];
+                aL[i] = bL[i];
+                pair_acc(aH[i], aL[i], -dep[i]);
+                pair_acc(aH[i], aL[i], xc[2 * NC * kT + t - 1]);
+                pair_acc(aH[i], aL[i], xc[3 * NC * kT + t + 1]);
+                // row crow+1: its old density, then the first arrivals
+                bH[i] = Rh2[i * CW + cc];
+                bL[i] = RL[(((q + 1) & 3) * NC + i) * CW + cc];
+                pair_acc(bH[i], bL[i], xc[4 * NC * kT + t - 1]);
+                pair_acc(bH[i], bL[i], own2[i]);
+                pair_acc(bH[i], bL[i], xc[5 * NC * kT + t + 1]);
             }
         }
     }
     if (mass_partials) {
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
-            double v = (double)msum[i] + (double)mcmp[i];
+            double v = (double)MS[(0 * NC + i) * kT + t] + (double)MS[(1 * NC + i) * kT + t];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
             if ((t & 31) == 0) RED[(t >> 5) * NC + i] = v;
@@ -649,6 +647,7 @@ __global__ void k_density(const Params P, const S *__restrict__ g, S *__restrict
 }
 
 struct Ops {
+    int wmax;
     int (*density)(const Params &, StateBufs, cudaStream_t);
     int (*step)(const Params &, const FusedGeom &, StateBufs, StateBufs, double *, cudaStream_t);
     size_t (*smem)(int W);
@@ -662,8 +661,9 @@ template <int NC, typename S, typename E> struct Impl {
     static auto kernel()
     {
         if constexpr (k64) return k_fused<NC, double, double>;
-        else return k_fused32<NC, E>;
+        else return k_fused32<NC, E, long long>;
     }
+    static constexpr int wmax() { return k64 ? kWmax : kWmax32; }
     static int density(const Params &P, StateBufs st, cudaStream_t s)
     {
         if constexpr (k64) {
@@ -683,8 +683,12 @@ template <int NC, typename S, typename E> struct Impl {
         // the limit is the widest strip's need, so that problems of other
         // widths launched later keep fitting under it
         if (cudaFuncSetAttribute(kernel(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem(kWmax)) != cudaSuccess)
+                                 (int)smem(wmax())) != cudaSuccess)
             return 0;
+        if constexpr (!k64)
+            if (cudaFuncSetAttribute(k_fused32<NC, E, int>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem(wmax())) != cudaSuccess)
+                return 0;
         int n = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel(), kT, bytes) != cudaSuccess)
             return 0;
@@ -698,16 +702,18 @@ template <int NC, typename S, typename E> struct Impl {
             k_fused<NC, double, double><<<grid, kT, g.smem, s>>>(
                 P, g.strip, g.seg_h, (const double *)in.g, (double *)out.g, in.rhi_d(),
                 out.rhi_d(), mp);
+        else if ((long long)NC * 8 * P.N < (1LL << 31))
+            k_fused32<NC, E, int><<<grid, kT, g.smem, s>>>(P, g.strip, g.seg_h, in, out, mp);
         else
-            k_fused32<NC, E><<<grid, kT, g.smem, s>>>(P, g.strip, g.seg_h, in, out, mp);
+            k_fused32<NC, E, long long><<<grid, kT, g.smem, s>>>(P, g.strip, g.seg_h, in, out, mp);
         return (int)cudaGetLastError();
     }
 };
 
 template <int NC, typename S, typename E> const Ops *ops_of()
 {
-    static const Ops o = {&Impl<NC, S, E>::density, &Impl<NC, S, E>::step, &Impl<NC, S, E>::smem,
-                          &Impl<NC, S, E>::occupancy};
+    static const Ops o = {Impl<NC, S, E>::wmax(), &Impl<NC, S, E>::density, &Impl<NC, S, E>::step,
+                          &Impl<NC, S, E>::smem, &Impl<NC, S, E>::occupancy};
     return &o;
 }
 
