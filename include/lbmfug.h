@@ -180,6 +180,28 @@ int lbm_synchronize(lbm_problem *p);
 /* Release the handle and its device memory.  NULL-safe. */
 int lbm_destroy(lbm_problem *p);
 
+/*
+ * Per-component sums out[i] = sum_{r < n} field[i * n + r] of a caller-owned
+ * binary64 device array field[nc][n] (for example the densities written by
+ * lbm_moments_device), into the caller's device array out[nc], enqueued on
+ * `stream` (a cudaStream_t; NULL = the legacy default stream).  The paper
+ * has no counterpart: this is a service for callers that cannot allocate
+ * device memory at the point where they need the reduction (a foreign
+ * memory pool owns the device, or a host callback or real-time loop cannot
+ * take the synchronisation of cudaMalloc).  It allocates nothing: the
+ * per-block partial sums live in a fixed scratch area inside the library
+ * (1216 * LBM_MAX_NC doubles, about 152 KB, held on every device that loads
+ * the library until the process exits).  The summation order is the same
+ * fixed order as lbm_mass.  If d_nonfinite is not NULL it receives 1 when a
+ * non-finite value was seen, else 0.  Returns LBM_EINVAL for NULL pointers,
+ * n < 1, or nc outside 1..LBM_MAX_NC (the scratch capacity).  The first call
+ * on a device looks up the scratch address and should come before any
+ * stream capture.  Calls share the scratch: calls that can overlap on the
+ * GPU race.
+ */
+int lbm_field_sums_noalloc(const double *d_field, int nc, long long n, double *d_out,
+                           int *d_nonfinite, void *stream);
+
 /* Lattice description: D, Q and the velocities e[Q][3] used by get/set_state. */
 int lbm_lattice_velocities(int lattice, int *D, int *Q, int *e);
 

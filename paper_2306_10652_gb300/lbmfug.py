@@ -66,6 +66,7 @@ _sig("lbm_set_state", ctypes.c_int, _vp, _dp, ctypes.c_size_t)
 _sig("lbm_step_count", ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_longlong))
 _sig("lbm_monitor", ctypes.c_int, _vp, _dp, ctypes.POINTER(ctypes.c_longlong), _ip)
 _sig("lbm_launch_count", ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_longlong))
+_sig("lbm_field_sums_noalloc", ctypes.c_int, _vp, ctypes.c_int, ctypes.c_longlong, _vp, _vp, _vp)
 _sig("lbm_synchronize", ctypes.c_int, _vp)
 _sig("lbm_destroy", ctypes.c_int, _vp)
 _sig("lbm_lattice_velocities", ctypes.c_int, ctypes.c_int, _ip, _ip, _ip)
@@ -74,7 +75,7 @@ _sig("lbm_strerror", ctypes.c_char_p, ctypes.c_int)
 EXPORTED = ["lbm_options_default", "lbm_create", "lbm_set_options", "lbm_init_fields",
             "lbm_init_fields_device", "lbm_step", "lbm_moments", "lbm_moments_device", "lbm_mass",
             "lbm_convergence", "lbm_get_state", "lbm_set_state", "lbm_step_count", "lbm_monitor",
-            "lbm_launch_count",
+            "lbm_launch_count", "lbm_field_sums_noalloc",
             "lbm_synchronize", "lbm_destroy", "lbm_lattice_velocities", "lbm_strerror"]
 
 
@@ -111,6 +112,18 @@ def _dev(t):
     if not (t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float64"):
         raise ValueError("device buffers must be contiguous float64 CUDA tensors")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def lbm_field_sums_noalloc(d_field, nc, n, d_out, d_nonfinite=None, stream=None):
+    """Per-component sums of a device field[nc][n] into device out[nc], with no
+    device allocation (see the C declaration).  Device buffers are torch CUDA
+    tensors (float64 field and out, int32 flag); stream is a raw cudaStream_t."""
+    if d_nonfinite is not None and not (d_nonfinite.is_cuda and str(d_nonfinite.dtype) == "torch.int32"):
+        raise ValueError("d_nonfinite must be an int32 CUDA tensor")
+    _check(_lib.lbm_field_sums_noalloc(_dev(d_field), int(nc), int(n), _dev(d_out),
+                                       None if d_nonfinite is None else ctypes.c_void_p(d_nonfinite.data_ptr()),
+                                       None if stream is None else ctypes.c_void_p(int(stream))),
+           "lbm_field_sums_noalloc")
 
 
 def lbm_lattice_velocities(lattice: int):
