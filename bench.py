@@ -49,6 +49,19 @@ def initial_density(d, case, nx, ny, seed=2):
     return (rho * synth.multiplicative_noise(seed, rho.shape, 0.01))[:, None]  # [nc, 1, ny, nx]
 
 
+# DRAM bytes per node-step of the fused binary32 step at Nc = 10, from the ncu
+# capture summarised in profiles/fused32_fp32_spinodal2048_nc10.md (2048 x 512
+# case: dram read + write = 837.4 MB over 1,048,576 nodes).  The traffic is
+# per node (strip/segment halos come from L2), so it scales with the nodes of
+# a launch.  None for any other form or Nc, or once the kernel changes.
+NCU_TRAFFIC_B_PER_NODE = {("fp32", "auto", 10): 837.39e6 / 1048576}
+
+
+def traffic_per_launch(args, nc, N):
+    v = NCU_TRAFFIC_B_PER_NODE.get((args.precision, args.schedule, nc))
+    return None if v is None else v * N
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
@@ -182,6 +195,15 @@ def run_gpu(args):
             dist.destroy_process_group()
         return None
     cpu = cpu_baseline(case, nx, ny, rho) if (ws == 1 and not args.no_cpu_baseline) else None
+    forms = None
+    if not args.no_forms:
+        forms = {}
+        for name, pr, sc, k in (("fp32dev_fused", lbmfug.LBM_FP32DEV, lbmfug.LBM_SCHED_AUTO, 6),
+                                ("fp64_fused", lbmfug.LBM_FP64, lbmfug.LBM_SCHED_AUTO, 4),
+                                ("fp64_threepass", lbmfug.LBM_FP64, lbmfug.LBM_SCHED_THREEPASS, 4)):
+            if pr == prec and sc == sched:
+                continue
+            forms[name] = time_form(lbmfug, case, rho, nx, ny, pr, sc, k, 2, local)
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
@@ -194,8 +216,10 @@ def run_gpu(args):
                    "parallelism": f"replicas{ws}" if ws > 1 else "single",
                    "l2": "inputs larger than L2 (populations %.2f GB per buffer)" % (9 * nc * spop * N / 1e9)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / pk["hbm_gbs"], "traffic": None,
-                     "peak_kind": pk_kind, "algorithmic_bytes_per_node_step": 2 * 9 * nc * spop},
+                     "frac": achieved / pk["hbm_gbs"], "traffic": traffic_per_launch(args, nc, N),
+                     "peak_kind": pk_kind, "algorithmic_bytes_per_node_step": 2 * 9 * nc * spop,
+                     "kernel": "fused step (k_fused32 / k_fused), one launch per step"},
+        "forms": forms,
         "gpu_launches": launches,
         "mass_monitor": {"at_step": at, "nonfinite": nonfinite,
                          "mass": None if mass is None else [float(v) for v in mass]},
@@ -204,6 +228,29 @@ def run_gpu(args):
     if ws > 1:
         dist.destroy_process_group()
     return line
+
+
+def time_form(lbmfug, case, rho, nx, ny, prec, sched, steps, warmup, local):
+    """Nc-GLUPS of one precision/schedule form on the same workload (CUDA events)."""
+    import torch
+    stream = torch.cuda.Stream()
+    prob = lbmfug.Problem(0, nx, ny, 1, case["a"], case["b"], case["omega"], np.asarray(case["kij"]),
+                          case["T"], case["tau"], precision=prec, schedule=sched,
+                          kappa_ref=case["kappa_ref"], stream=stream.cuda_stream, monitor_every=1)
+    d_rho = torch.from_numpy(rho.reshape(-1)).to(f"cuda:{local}")
+    prob.init_fields_device(d_rho)
+    del d_rho
+    prob.step(warmup)
+    prob.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    prob.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    prob.close()
+    ms = e0.elapsed_time(e1)
+    return {"value": case["nc"] * nx * ny * steps / (ms * 1e-3) / 1e9, "ms_per_step": ms / steps}
 
 
 def run_e2e(args, lbmfug, case, rho, nx, ny, prec, sched, local):
@@ -292,7 +339,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--nc", type=int, default=10)
-    ap.add_argument("--precision", default="fp32dev", choices=["fp32dev", "fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32dev", "fp32", "fp64"])
+    ap.add_argument("--no-forms", action="store_true", help="skip the comparison forms")
     ap.add_argument("--grid", default=None, help="NXxNY override of the workload grid (profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--schedule", default="auto", choices=["auto", "threepass", "fused"])

@@ -37,15 +37,25 @@ size_t max_optin_smem()
     return (size_t)v;
 }
 
-__global__ void k_mass_final(int nc, int nblocks, const double *__restrict__ partials,
-                             double *__restrict__ out, int *__restrict__ nonfinite)
+// One block per component: threads sum strided partials, then a fixed-order
+// warp-shuffle and shared-memory tree (deterministic for a given geometry).
+__global__ void __launch_bounds__(256) k_mass_final(int nc, int nblocks, const double *__restrict__ partials,
+                                                    double *__restrict__ out, int *__restrict__ nonfinite)
 {
-    const int i = threadIdx.x;
-    if (i >= nc) return;
+    __shared__ double sh[8];
+    const int i = blockIdx.x;
     double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += partials[(long long)b * nc + i];
-    out[i] = s;
-    if (!isfinite(s)) atomicExch(nonfinite, 1);
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partials[(long long)b * nc + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        out[i] = t;
+        if (!isfinite(t)) atomicExch(nonfinite, 1);
+    }
 }
 
 }  // namespace
@@ -93,7 +103,7 @@ int launch_fused_step(int prec, int nc, const Params &P, const FusedGeom &geo, S
 int launch_fused_mass_final(int nc, const FusedGeom &geo, const double *partials, double *out,
                             int *nonfinite, cudaStream_t s)
 {
-    k_mass_final<<<1, 32, 0, s>>>(nc, geo.nstrips * geo.segs, partials, out, nonfinite);
+    k_mass_final<<<nc, 256, 0, s>>>(nc, geo.nstrips * geo.segs, partials, out, nonfinite);
     return (int)cudaGetLastError();
 }
 
