@@ -195,6 +195,8 @@ def run_gpu(args):
             dist.destroy_process_group()
         return None
     cpu = cpu_baseline(case, nx, ny, rho) if (ws == 1 and not args.no_cpu_baseline) else None
+    batched = run_batched(args, lbmfug, local) if not args.no_batched else None
+    served = run_served(args, lbmfug) if not args.no_served else None
     forms = None
     if not args.no_forms:
         forms = {}
@@ -220,6 +222,8 @@ def run_gpu(args):
                      "peak_kind": pk_kind, "algorithmic_bytes_per_node_step": 2 * 9 * nc * spop,
                      "kernel": "fused step (k_fused32 / k_fused), one launch per step"},
         "forms": forms,
+        "batched": batched,
+        "served": served,
         "gpu_launches": launches,
         "mass_monitor": {"at_step": at, "nonfinite": nonfinite,
                          "mass": None if mass is None else [float(v) for v in mass]},
@@ -303,6 +307,140 @@ def cpu_baseline(case, nx, ny, rho, target_s=12.0):
             "sample": f"{crop}x{crop} crop of the workload, {steps} steps ({dt:.1f} s), single thread"}
 
 
+TERNARY_FILE = os.path.join(ROOT, "paper_2306_10652_gb300", "workloads", "ternary_sweep.json")
+
+
+def ternary_jobs(limit=None):
+    """The batched sweep's slabs: Eq. (15) profiles at the stored flash densities."""
+    d = json.load(open(TERNARY_FILE))
+    jobs = []
+    for jb in d["jobs"][:limit]:
+        nx, ny, SV, W = jb["nx"], jb["ny"], jb["S_V"], d["W"]
+        x = np.arange(nx, dtype=float)
+        rv = np.asarray(jb["rhoi_V"])[:, None]
+        rl = np.asarray(jb["rhoi_L"])[:, None]
+        prof = rv + 0.5 * (rl - rv) * (np.tanh(2 * (x - 0.5 * SV * nx) / W)
+                                       - np.tanh(2 * (x - (1 - 0.5 * SV) * nx) / W))
+        jobs.append((jb["T"], np.repeat(prof[:, None, :], ny, axis=1)))
+    return d, jobs
+
+
+def run_batched(args, lbmfug, local):
+    """Batched form: all sweep slabs to convergence (solves/s), and the plain
+    binary64 per-problem path timed on a sample of the same slabs."""
+    import torch
+    d, jobs = ternary_jobs(args.batch_jobs)
+    # binary32 storage jitters at the resolution of its populations: converged
+    # = largest density change below 2e-6 per 1000 steps (~8 ulp at rho ~ 2)
+    tol, every, cap = 2e-6, 1000, args.batch_max_steps
+    t0 = time.perf_counter()
+    with lbmfug.Batch(d["a"], d["b"], d["omega"], np.asarray(d["kij"]), d["tau"], jobs,
+                      precision=lbmfug.LBM_FP32, kappa_ref=d["kappa_ref"]) as bt:
+        t1 = time.perf_counter()
+        done = bt.run(cap, every, tol)
+        t2 = time.perf_counter()
+        states = [bt.state(k) for k in range(len(jobs))]
+        info = bt.info()
+    conv = sum(s["converged"] for s in states)
+    failed = sum(s["failed"] for s in states)
+    node_steps = sum(s["steps"] * r.shape[1] * r.shape[2] for s, (_, r) in zip(states, jobs))
+    wall = t2 - t1
+    # binary64 single-problem path, one problem at a time, on a sample of the slabs
+    sample = sorted(range(len(jobs)), key=lambda k: jobs[k][1].shape[2])[:: max(1, len(jobs) // 6)]
+    fp64_ms = {}
+    for k in sample:
+        T, rho = jobs[k]
+        p = lbmfug.Problem(0, rho.shape[2], rho.shape[1], 1, d["a"], d["b"], d["omega"], np.asarray(d["kij"]),
+                           T, d["tau"], precision=lbmfug.LBM_FP64, kappa_ref=d["kappa_ref"])
+        p.init_fields(rho[:, None])
+        p.step(200)
+        p.synchronize()
+        e0 = time.perf_counter()
+        p.step(2000)
+        p.synchronize()
+        fp64_ms[rho.shape[2]] = (time.perf_counter() - e0) / 2000 * 1e3
+        p.close()
+    sizes = sorted(fp64_ms)
+    est_fp64 = 0.0
+    for s, (_, r) in zip(states, jobs):
+        if s["converged"]:
+            est_fp64 += s["steps"] * float(np.interp(r.shape[2], sizes, [fp64_ms[v] for v in sizes])) * 1e-3
+    return {"jobs": len(jobs), "converged": conv, "failed": failed, "criterion": f"max|drho| < {tol} per {every} steps",
+            "max_steps": cap, "wall_s": wall, "setup_s": t1 - t0, "solves_per_s": conv / wall,
+            "node_steps_per_s": node_steps / wall, "threads": info["threads"], "ctas": info["ctas"],
+            "rounds": info["rounds"], "precision": "fp32",
+            "fp64_per_problem": {"ms_per_step_by_nx": fp64_ms,
+                                 "estimated_solves_per_s": conv / est_fp64 if est_fp64 > 0 else None}}
+
+
+SERVE_FILE = os.path.join(ROOT, "paper_2306_10652_gb300", "workloads", "served_requests.json")
+
+
+def served_field(r, W):
+    """Initial densities of one request: Eq. (15) slab along x (D2Q9 or a D3Q19
+    box), or Eq. (13) droplet with the liquid area fraction 1 - S_V."""
+    nx, ny, nz, SV = r["nx"], r["ny"], r["nz"], r["S_V"]
+    rv = np.asarray(r["rhoi_V"])[:, None, None, None]
+    rl = np.asarray(r["rhoi_L"])[:, None, None, None]
+    z, y, x = np.meshgrid(np.arange(nz, dtype=float), np.arange(ny, dtype=float), np.arange(nx, dtype=float),
+                          indexing="ij")
+    if r["kind"] == "droplet":
+        R = np.sqrt((1.0 - SV) * nx * ny / np.pi)
+        dist = np.sqrt((x - nx / 2) ** 2 + (y - ny / 2) ** 2) - R
+        return 0.5 * (rl + rv) - 0.5 * (rl - rv) * np.tanh(2 * dist / W)
+    return rv + 0.5 * (rl - rv) * (np.tanh(2 * (x - 0.5 * SV * nx) / W) - np.tanh(2 * (x - (1 - 0.5 * SV) * nx) / W))
+
+
+def run_served(args, lbmfug):
+    """Served form: the requests arrive with their Poisson gaps, run to
+    convergence under the 80 % memory budget; latency percentiles, solves/s,
+    and the plain binary64 path run one request at a time (estimated from
+    its measured per-step time for every request)."""
+    d = json.load(open(SERVE_FILE))
+    reqs = d["requests"]
+    tol, every, cap = 2e-6, 1000, args.serve_max_steps
+    fields = [served_field(r, d["W"]) for r in reqs]
+    with lbmfug.Server(0.8, max_active=args.serve_slots) as srv:
+        t0 = time.perf_counter()
+        ids = []
+        for r, rho in zip(reqs, fields):
+            time.sleep(r["arrival_gap_s"])
+            ids.append(srv.submit(r["lattice"], r["a"], r["b"], r["omega"], np.asarray(r["kij"]), r["T"], d["tau"],
+                                  rho, precision=lbmfug.LBM_FP32DEV, check_every=every, max_steps=cap, tol=tol,
+                                  kappa_ref=d["kappa_ref"]))
+        srv.wait_all()
+        t1 = time.perf_counter()
+        polls = [srv.poll(j) for j in ids]
+        stats = srv.stats()
+    lat = np.array([p["latency_s"] for p in polls])
+    done = [p for p in polls if p["state"] in ("converged", "exhausted")]
+    conv = sum(p["state"] == "converged" for p in polls)
+    work = sum(p["steps"] * r["nc"] * r["nx"] * r["ny"] * r["nz"] for p, r in zip(polls, reqs))
+    # binary64 per-request path: each request alone, per-step time measured on 20 steps
+    est = 0.0
+    for p, r, rho in zip(polls, reqs, fields):
+        prob = lbmfug.Problem(r["lattice"], r["nx"], r["ny"], r["nz"], r["a"], r["b"], r["omega"],
+                              np.asarray(r["kij"]), r["T"], d["tau"], precision=lbmfug.LBM_FP64,
+                              kappa_ref=d["kappa_ref"])
+        prob.init_fields(rho)
+        prob.step(5)
+        prob.synchronize()
+        e0 = time.perf_counter()
+        prob.step(20)
+        prob.synchronize()
+        est += (time.perf_counter() - e0) / 20 * p["steps"]
+        prob.close()
+    return {"requests": len(reqs), "converged": conv, "finished": len(done),
+            "failed": sum(p["state"] == "failed" for p in polls),
+            "criterion": f"max|drho| < {tol} per {every} steps, cap {cap} steps",
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "wall_s": t1 - t0, "solves_per_s": len(done) / (t1 - t0),
+            "nc_node_steps_per_s": work / (t1 - t0), "slots": args.serve_slots,
+            "peak_bytes": stats["peak_bytes"], "budget_bytes": stats["budget_bytes"], "rounds": stats["rounds"],
+            "precision": "fp32dev (binary32 populations, binary64 EOS and forces)",
+            "fp64_one_at_a_time": {"estimated_wall_s": est, "estimated_solves_per_s": len(done) / est if est else None}}
+
+
 def run_reference(args):
     ws, rank, _ = dist_setup()
     if rank != 0:
@@ -343,6 +481,12 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the comparison forms")
     ap.add_argument("--grid", default=None, help="NXxNY override of the workload grid (profiling)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-jobs", type=int, default=None, help="first N jobs of the sweep")
+    ap.add_argument("--batch-max-steps", type=int, default=400000)
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-max-steps", type=int, default=20000)
     ap.add_argument("--schedule", default="auto", choices=["auto", "threepass", "fused"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

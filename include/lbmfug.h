@@ -202,6 +202,111 @@ int lbm_destroy(lbm_problem *p);
 int lbm_field_sums_noalloc(const double *d_field, int nc, long long n, double *d_out,
                            int *d_nonfinite, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batched form: many small independent D2Q9 problems (for example the
+ * points of a ternary-diagram sweep, each a flat-interface slab at its own
+ * temperature, as in the paper's Sec. 3.3) sharing the components' PR
+ * parameters.  One persistent kernel advances all of them, a round of
+ * `check_every` steps per problem per launch, replayed from a captured CUDA
+ * graph; every round each problem's densities are compared with those at
+ * the start of the round and a problem whose largest change is below `tol`
+ * is finished and skipped from then on.  Storage is the binary32 format of
+ * LBM_FP32DEV/LBM_FP32 (opt->precision selects binary64 or binary32
+ * thermodynamics; LBM_FP64 is taken as LBM_FP32DEV).  The CTA size is chosen
+ * by timed trials on the first creation for a given (precision, Nc, largest
+ * box) and cached for the process; results do not depend on it.
+ * ------------------------------------------------------------------------ */
+typedef struct lbm_job {
+    int nx, ny;          /* periodic box, nx * ny <= 2^20 and fitting shared memory */
+    double T;            /* temperature (lattice units) */
+    const double *rho;   /* initial mass densities [Nc][ny][nx] (host, > 0) */
+} lbm_job;
+
+typedef struct lbm_batch lbm_batch;
+
+/* Nc in 1..10; a, b, omega, kij (NULL = 0) and tau as lbm_create; opt may be
+ * NULL (defaults; opt->M, R, kappa_ref, kappa_ref_index, stream are used). */
+int lbm_batch_create(lbm_batch **out, int Nc, const double *a, const double *b, const double *omega,
+                     const double *kij, double tau, const lbm_options *opt, const lbm_job *jobs,
+                     int njobs);
+
+/* Run rounds of check_every steps until every problem has finished or
+ * max_steps steps have been taken.  A problem finishes when the largest
+ * change of its densities over a round is below tol (converged) or when a
+ * density is not finite (failed; it is retired and the others go on).
+ * *n_converged receives the number of finished problems.  Synchronises. */
+int lbm_batch_run(lbm_batch *b, long long max_steps, int check_every, double tol, int *n_converged);
+
+/* State of problem `job`: densities rho[Nc][ny][nx] (host, may be NULL), steps
+ * taken, the largest density change of its last round, and *converged =
+ * 0 running, 1 converged, 2 failed. */
+int lbm_batch_job_state(lbm_batch *b, int job, double *rho, long long *steps, double *last_drho,
+                        int *converged);
+
+/* Launch geometry chosen by the tuner, rounds run and kernels launched. */
+int lbm_batch_info(const lbm_batch *b, int *threads, int *ctas, long long *rounds,
+                   long long *launches);
+
+/* Override the CTA size (128, 256 or 512 threads). */
+int lbm_batch_set_threads(lbm_batch *b, int threads);
+
+int lbm_batch_destroy(lbm_batch *b);
+
+/* ------------------------------------------------------------------------
+ * Served form: a request loop over phase-equilibrium jobs (a problem run
+ * "to equilibrium" as in the paper's Sec. 3, Eqs. 1-12).  Requests of any
+ * lattice, size, Nc and (T, composition) arrive at any time; a worker thread
+ * admits them in arrival order while the estimated device bytes of the
+ * running jobs stay within hbm_budget_frac of the device memory and fewer
+ * than max_active jobs run; every running job is its own problem on its own
+ * stream, advanced in rounds of check_every steps whose kernels overlap on
+ * the GPU; a job finishes when the largest density change over a round is
+ * below tol (converged), when a density is not finite (failed) or after
+ * max_steps steps (exhausted), and its memory goes to the next request.
+ * ------------------------------------------------------------------------ */
+typedef struct lbm_request {
+    int lattice, nx, ny, nz, Nc;          /* as lbm_create */
+    const double *a, *b, *omega, *kij;    /* kij may be NULL */
+    const double *M;                      /* molar masses, NULL = 1 */
+    double T, tau, kappa_ref;             /* kappa_ref <= 0 = 0.02 */
+    const double *rho;                    /* initial densities [Nc][nz][ny][nx] (host; copied) */
+    int precision;                        /* enum lbm_precision */
+    int check_every;                      /* steps per round */
+    long long max_steps;
+    double tol;                           /* convergence: max |d rho| per round */
+} lbm_request;
+
+typedef struct lbm_server lbm_server;
+
+/* Device bytes a request of this size would hold while running. */
+int lbm_server_estimate_bytes(int lattice, int nx, int ny, int nz, int Nc, int precision, size_t *bytes);
+
+/* Start the request loop on the current device.  hbm_budget_frac in (0, 1]
+ * of the device's total memory (0.8 is the intended setting). */
+int lbm_server_create(lbm_server **out, double hbm_budget_frac, int max_active);
+
+/* Queue a request (inputs are copied; returns at once).  *id identifies it.
+ * LBM_ENOMEM if the request alone exceeds the budget. */
+int lbm_server_submit(lbm_server *s, const lbm_request *r, long long *id);
+
+/* *state: 0 queued, 1 running, 2 converged, 3 failed, 4 max_steps reached;
+ * latency (submit to finish, seconds; -1 while unfinished).  Returns the
+ * job's error status if it failed. */
+int lbm_server_poll(lbm_server *s, long long id, int *state, long long *steps, double *latency_s,
+                    double *last_drho);
+
+/* Final densities [Nc][nz][ny][nx] of a finished (state 2 or 4) request. */
+int lbm_server_result(lbm_server *s, long long id, double *rho);
+
+/* Block until every submitted request has finished. */
+int lbm_server_wait_all(lbm_server *s);
+
+int lbm_server_stats(lbm_server *s, long long *submitted, long long *completed, size_t *peak_bytes,
+                     double *budget_bytes, long long *rounds);
+
+/* Finish the queued and running requests, then stop the loop. */
+int lbm_server_destroy(lbm_server *s);
+
 /* Lattice description: D, Q and the velocities e[Q][3] used by get/set_state. */
 int lbm_lattice_velocities(int lattice, int *D, int *Q, int *e);
 

@@ -185,7 +185,10 @@ def rachford_rice(z, K):
     lo = 1.0 / (1.0 - kmax)
     hi = 1.0 / (1.0 - kmin)
     eps = 1e-14 * (hi - lo)
-    return brentq(f, lo + eps, hi - eps, xtol=1e-16, rtol=1e-15, maxiter=500)
+    try:
+        return brentq(f, lo + eps, hi - eps, xtol=1e-16, rtol=1e-15, maxiter=500)
+    except ValueError:
+        return None  # no sign change resolvable between the asymptotes
 
 
 class FlashResult(dict):

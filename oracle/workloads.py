@@ -29,9 +29,9 @@ def two_phase_interval(P: OracleProblem, z, npts=600, pmin=1e-6, pmax=1.0):
     return ps[max(idx[0] - 1, 0)], ps[min(idx[-1] + 1, npts - 1)], ps[idx[0]], ps[idx[-1]]
 
 
-def two_phase_pressure(P: OracleProblem, z, SV=0.5, tol=1e-10):
+def two_phase_pressure(P: OracleProblem, z, SV=0.5, tol=1e-10, npts=600):
     """Pressure with flash vapour volume fraction S_V = SV, and the flash there."""
-    iv = two_phase_interval(P, z)
+    iv = two_phase_interval(P, z, npts=npts)
     if iv is None:
         return None
     _, _, lo, hi = iv

@@ -67,6 +67,36 @@ _sig("lbm_step_count", ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_longlong))
 _sig("lbm_monitor", ctypes.c_int, _vp, _dp, ctypes.POINTER(ctypes.c_longlong), _ip)
 _sig("lbm_launch_count", ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_longlong))
 _sig("lbm_field_sums_noalloc", ctypes.c_int, _vp, ctypes.c_int, ctypes.c_longlong, _vp, _vp, _vp)
+class lbm_job(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("T", ctypes.c_double), ("rho", _dp)]
+
+
+_sig("lbm_batch_create", ctypes.c_int, ctypes.POINTER(_vp), ctypes.c_int, _dp, _dp, _dp, _dp, ctypes.c_double,
+     ctypes.POINTER(lbm_options), ctypes.POINTER(lbm_job), ctypes.c_int)
+_sig("lbm_batch_run", ctypes.c_int, _vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_double, _ip)
+_sig("lbm_batch_job_state", ctypes.c_int, _vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_longlong), _dp, _ip)
+_sig("lbm_batch_info", ctypes.c_int, _vp, _ip, _ip, ctypes.POINTER(ctypes.c_longlong),
+     ctypes.POINTER(ctypes.c_longlong))
+_sig("lbm_batch_set_threads", ctypes.c_int, _vp, ctypes.c_int)
+_sig("lbm_batch_destroy", ctypes.c_int, _vp)
+class lbm_request(ctypes.Structure):
+    _fields_ = [("lattice", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("Nc", ctypes.c_int), ("a", _dp), ("b", _dp), ("omega", _dp), ("kij", _dp), ("M", _dp),
+                ("T", ctypes.c_double), ("tau", ctypes.c_double), ("kappa_ref", ctypes.c_double),
+                ("rho", _dp), ("precision", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("max_steps", ctypes.c_longlong), ("tol", ctypes.c_double)]
+
+
+_sig("lbm_server_estimate_bytes", ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+     ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t))
+_sig("lbm_server_create", ctypes.c_int, ctypes.POINTER(_vp), ctypes.c_double, ctypes.c_int)
+_sig("lbm_server_submit", ctypes.c_int, _vp, ctypes.POINTER(lbm_request), ctypes.POINTER(ctypes.c_longlong))
+_sig("lbm_server_poll", ctypes.c_int, _vp, ctypes.c_longlong, _ip, ctypes.POINTER(ctypes.c_longlong), _dp, _dp)
+_sig("lbm_server_result", ctypes.c_int, _vp, ctypes.c_longlong, _dp)
+_sig("lbm_server_wait_all", ctypes.c_int, _vp)
+_sig("lbm_server_stats", ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+     ctypes.POINTER(ctypes.c_size_t), _dp, ctypes.POINTER(ctypes.c_longlong))
+_sig("lbm_server_destroy", ctypes.c_int, _vp)
 _sig("lbm_synchronize", ctypes.c_int, _vp)
 _sig("lbm_destroy", ctypes.c_int, _vp)
 _sig("lbm_lattice_velocities", ctypes.c_int, ctypes.c_int, _ip, _ip, _ip)
@@ -75,7 +105,10 @@ _sig("lbm_strerror", ctypes.c_char_p, ctypes.c_int)
 EXPORTED = ["lbm_options_default", "lbm_create", "lbm_set_options", "lbm_init_fields",
             "lbm_init_fields_device", "lbm_step", "lbm_moments", "lbm_moments_device", "lbm_mass",
             "lbm_convergence", "lbm_get_state", "lbm_set_state", "lbm_step_count", "lbm_monitor",
-            "lbm_launch_count", "lbm_field_sums_noalloc",
+            "lbm_launch_count", "lbm_field_sums_noalloc", "lbm_batch_create", "lbm_batch_run",
+            "lbm_batch_job_state", "lbm_batch_info", "lbm_batch_set_threads", "lbm_batch_destroy",
+            "lbm_server_estimate_bytes", "lbm_server_create", "lbm_server_submit", "lbm_server_poll",
+            "lbm_server_result", "lbm_server_wait_all", "lbm_server_stats", "lbm_server_destroy",
             "lbm_synchronize", "lbm_destroy", "lbm_lattice_velocities", "lbm_strerror"]
 
 
@@ -268,3 +301,171 @@ class Problem:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Batch:
+    """Many small D2Q9 problems advanced together (the lbm_batch_* calls).
+
+    ``jobs`` is a list of (T, rho[Nc, ny, nx]) pairs; the components' PR
+    parameters, tau and the options are shared.
+    """
+
+    def __init__(self, a, b, omega, kij, tau, jobs, *, precision=LBM_FP32, kappa_ref=0.02,
+                 kappa_ref_index=0, M=None, R=1.0, stream=None):
+        self._h = None
+        a = _host(a)
+        self.nc = a.size
+        b = _host(b, self.nc)
+        omega = _host(omega, self.nc)
+        kij = None if kij is None else _host(kij, self.nc * self.nc)
+        opt = lbm_options()
+        _lib.lbm_options_default(ctypes.byref(opt))
+        opt.precision = int(precision)
+        opt.kappa_ref = float(kappa_ref)
+        opt.kappa_ref_index = int(kappa_ref_index)
+        self._M = None if M is None else _host(M, self.nc)
+        opt.M = _hp(self._M)
+        opt.R = float(R)
+        opt.stream = None if stream is None else ctypes.c_void_p(int(stream))
+        self._rho = []
+        arr = (lbm_job * len(jobs))()
+        self.shapes = []
+        for k, (T, rho) in enumerate(jobs):
+            r = np.ascontiguousarray(rho, dtype=np.float64)
+            ny, nx = r.shape[-2], r.shape[-1]
+            r = r.reshape(self.nc, ny, nx)
+            self._rho.append(r)
+            self.shapes.append((ny, nx))
+            arr[k].nx, arr[k].ny, arr[k].T = nx, ny, float(T)
+            arr[k].rho = r.ctypes.data_as(_dp)
+        h = _vp()
+        _check(_lib.lbm_batch_create(ctypes.byref(h), self.nc, _hp(a), _hp(b), _hp(omega), _hp(kij),
+                                     float(tau), ctypes.byref(opt), arr, len(jobs)), "lbm_batch_create")
+        self._h = h
+        self._rho = None
+        self.njobs = len(jobs)
+
+    def run(self, max_steps, check_every=1000, tol=1e-10):
+        n = ctypes.c_int()
+        _check(_lib.lbm_batch_run(self._h, int(max_steps), int(check_every), float(tol), ctypes.byref(n)),
+               "lbm_batch_run")
+        return n.value
+
+    def state(self, job):
+        ny, nx = self.shapes[job]
+        rho = np.empty((self.nc, ny, nx))
+        steps = ctypes.c_longlong()
+        d = ctypes.c_double()
+        c = ctypes.c_int()
+        _check(_lib.lbm_batch_job_state(self._h, int(job), _hp(rho), ctypes.byref(steps), ctypes.byref(d),
+                                        ctypes.byref(c)), "lbm_batch_job_state")
+        return {"rho": rho, "steps": steps.value, "last_drho": d.value, "converged": c.value == 1,
+                "failed": c.value == 2}
+
+    def info(self):
+        th, ct = ctypes.c_int(), ctypes.c_int()
+        rd, ln = ctypes.c_longlong(), ctypes.c_longlong()
+        _check(_lib.lbm_batch_info(self._h, ctypes.byref(th), ctypes.byref(ct), ctypes.byref(rd),
+                                   ctypes.byref(ln)), "lbm_batch_info")
+        return {"threads": th.value, "ctas": ct.value, "rounds": rd.value, "launches": ln.value}
+
+    def set_threads(self, threads):
+        _check(_lib.lbm_batch_set_threads(self._h, int(threads)), "lbm_batch_set_threads")
+
+    def close(self):
+        if self._h is not None:
+            _lib.lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Server:
+    """Admission-controlled request loop (the lbm_server_* calls)."""
+
+    STATES = {0: "queued", 1: "running", 2: "converged", 3: "failed", 4: "exhausted"}
+
+    def __init__(self, hbm_budget_frac=0.8, max_active=8):
+        h = _vp()
+        _check(_lib.lbm_server_create(ctypes.byref(h), float(hbm_budget_frac), int(max_active)),
+               "lbm_server_create")
+        self._h = h
+        self._shapes = {}
+
+    def submit(self, lattice, a, b, omega, kij, T, tau, rho, *, precision=LBM_FP32DEV, check_every=1000,
+               max_steps=100000, tol=1e-10, M=None, kappa_ref=0.02):
+        a = _host(a)
+        nc = a.size
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        shape = rho.shape[1:] if rho.ndim == 4 else (1,) + rho.shape[1:]
+        nz, ny, nx = shape
+        keep = [a, _host(b, nc), _host(omega, nc), None if kij is None else _host(kij, nc * nc),
+                None if M is None else _host(M, nc), rho.reshape(-1)]
+        q = lbm_request(lattice=int(lattice), nx=nx, ny=ny, nz=nz, Nc=nc, a=_hp(keep[0]), b=_hp(keep[1]),
+                        omega=_hp(keep[2]), kij=_hp(keep[3]), M=_hp(keep[4]), T=float(T), tau=float(tau),
+                        kappa_ref=float(kappa_ref), rho=_hp(keep[5]), precision=int(precision),
+                        check_every=int(check_every), max_steps=int(max_steps), tol=float(tol))
+        jid = ctypes.c_longlong()
+        _check(_lib.lbm_server_submit(self._h, ctypes.byref(q), ctypes.byref(jid)), "lbm_server_submit")
+        self._shapes[jid.value] = (nc,) + tuple(shape)
+        return jid.value
+
+    def poll(self, jid):
+        st, steps = ctypes.c_int(), ctypes.c_longlong()
+        lat, d = ctypes.c_double(), ctypes.c_double()
+        rc = _lib.lbm_server_poll(self._h, int(jid), ctypes.byref(st), ctypes.byref(steps), ctypes.byref(lat),
+                                  ctypes.byref(d))
+        if rc == LBM_EINVAL:
+            raise LbmError(rc, "lbm_server_poll")
+        return {"state": self.STATES[st.value], "steps": steps.value, "latency_s": lat.value,
+                "last_drho": d.value, "status": rc}
+
+    def result(self, jid):
+        rho = np.empty(self._shapes[jid])
+        _check(_lib.lbm_server_result(self._h, int(jid), _hp(rho)), "lbm_server_result")
+        return rho
+
+    def wait_all(self):
+        _check(_lib.lbm_server_wait_all(self._h), "lbm_server_wait_all")
+
+    def stats(self):
+        sub, comp, rd = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        peak, bud = ctypes.c_size_t(), ctypes.c_double()
+        _check(_lib.lbm_server_stats(self._h, ctypes.byref(sub), ctypes.byref(comp), ctypes.byref(peak),
+                                     ctypes.byref(bud), ctypes.byref(rd)), "lbm_server_stats")
+        return {"submitted": sub.value, "completed": comp.value, "peak_bytes": peak.value,
+                "budget_bytes": bud.value, "rounds": rd.value}
+
+    def close(self):
+        if self._h is not None:
+            _lib.lbm_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def lbm_server_estimate_bytes(lattice, nx, ny, nz, nc, precision):
+    v = ctypes.c_size_t()
+    _check(_lib.lbm_server_estimate_bytes(int(lattice), int(nx), int(ny), int(nz), int(nc), int(precision),
+                                          ctypes.byref(v)), "lbm_server_estimate_bytes")
+    return v.value
