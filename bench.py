@@ -123,6 +123,21 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def aggregate_replicas(ms, units, world_size, device="cpu"):
+    """Replicas: the job time is the slowest rank's, the work is every rank's.
+    Returns (max ms over ranks, sum of units over ranks); one process = as is."""
+    if world_size <= 1:
+        return ms, units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    u = torch.tensor([float(units)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.barrier()
+    return float(t.item()), float(u.item())
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -174,14 +189,9 @@ def run_gpu(args):
     launches = prob.launch_count() - l0
     ms = e0.elapsed_time(e1)
     mass, at, nonfinite = prob.monitor()
-    if ws > 1:
-        t = torch.tensor([ms], device=f"cuda:{local}", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
-    prob.close()
     N = nx * ny
-    node_steps = N * args.steps * ws
+    ms, node_steps = aggregate_replicas(ms, N * args.steps, ws, device=f"cuda:{local}")
+    prob.close()
     value = nc * node_steps / (ms * 1e-3) / 1e9
     spop = 8 if prec == lbmfug.LBM_FP64 else 4
     alg_bytes_per_launch = 2 * 9 * nc * spop * N
