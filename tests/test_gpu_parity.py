@@ -83,6 +83,28 @@ def test_one_step_fp32(case):
     assert one_step_case(seed, nc, lattice, shape, tau, Mr, FP32, AUTO) < 1e-5
 
 
+STRIP_CASES = [
+    # seed, nc, shape (nz, ny, nx), steps: ragged strips and segments, periodic wrap
+    (90, 2, (1, 3, 300), 1),
+    (91, 3, (1, 130, 127), 1),
+    (92, 10, (1, 2, 253), 3),
+    (93, 7, (1, 64, 5), 1),
+    (94, 2, (1, 1, 1), 2),
+    (95, 9, (1, 37, 250), 2),
+    (96, 1, (1, 9, 250), 2),
+    (97, 16, (1, 5, 131), 1),
+]
+
+
+@pytest.mark.parametrize("case", STRIP_CASES, ids=lambda c: f"nc{c[1]}-{c[2][1]}x{c[2][2]}")
+def test_fp32_fused_strips(case):
+    """Binary32 fused kernels (all components of a column in one thread for
+    Nc = 1, split over two threads for Nc >= 2) against the oracle: within
+    1e-5 of max |g_i| after one to three steps."""
+    seed, nc, shape, steps = case
+    assert one_step_case(seed, nc, 0, shape, precision=FP32, schedule=AUTO, nsteps=steps) < 1e-5
+
+
 def test_ten_steps_fp64_two_phase():
     # liquid-range densities inside the two-phase region: strong forces
     assert one_step_case(11, 3, 0, (1, 24, 40), nsteps=10, lo=0.05, hi=0.6) < 1e-11
@@ -227,7 +249,7 @@ def test_zero_steps_and_step_count():
         assert gp.step_count() == 3
 
 
-@pytest.mark.parametrize("precision", [FP64, FP32DEV])
+@pytest.mark.parametrize("precision", [FP64, FP32DEV, FP32])
 def test_monitor_matches_mass(precision):
     """The fused per-step mass monitor equals the separate reduction."""
     shape = (1, 37, 300)
