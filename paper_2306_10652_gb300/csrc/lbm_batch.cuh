@@ -80,7 +80,7 @@ __device__ __forceinline__ void job_lnf(const Shared &S, const Job &J, const E (
     E rho = 0;
 #pragma unroll
     for (int i = 0; i < NC; ++i) rho += rm[i];
-    const E inv = (E)1 / rho;
+    const E inv = tdiv((E)1, rho);
     E x[NC];
 #pragma unroll
     for (int i = 0; i < NC; ++i) x[i] = rm[i] * inv;
@@ -102,14 +102,14 @@ __device__ __forceinline__ void job_lnf(const Shared &S, const Job &J, const E (
     const E B = bm * rho;
     const E omB = (E)1 - B;
     const E den = fma(B, (E)2 - B, (E)1);
-    const E Zm1 = B / omB - am * rho / RT / den;
-    const E Lr = log(fma((E)1 + kSqrt2, B, (E)1) / fma((E)1 - kSqrt2, B, (E)1));
-    const E C0 = (E)J.lnRT - log(omB);
-    const E invbm = (E)1 / bm;
-    const E C1 = Zm1 * invbm + am * Lr * invbm * invbm / ((E)2 * kSqrt2 * RT);
-    const E C2 = -Lr * invbm / (kSqrt2 * RT);
+    const E Zm1 = tdiv(B, omB) - tdiv(tdiv(am * rho, RT), den);
+    const E Lr = tlog(tdiv(fma((E)1 + kSqrt2, B, (E)1), fma((E)1 - kSqrt2, B, (E)1)));
+    const E C0 = (E)J.lnRT - tlog(omB);
+    const E invbm = tdiv((E)1, bm);
+    const E C1 = Zm1 * invbm + tdiv(am * Lr * invbm * invbm, (E)2 * kSqrt2 * RT);
+    const E C2 = tdiv(-Lr * invbm, kSqrt2 * RT);
 #pragma unroll
-    for (int i = 0; i < NC; ++i) lnf[i] = log(rm[i]) + C0 + fma((E)S.b[i], C1, Sv[i] * C2);
+    for (int i = 0; i < NC; ++i) lnf[i] = tlog(rm[i]) + C0 + fma((E)S.b[i], C1, Sv[i] * C2);
 }
 
 template <int NC, typename E>
@@ -212,7 +212,7 @@ __global__ void k_batch_round(const Shared S, const Job *__restrict__ jobs, Stat
                     Fx[i] = (float)fx;
                     Fy[i] = (float)fy;
                 }
-                const E irt = (E)1 / rt;
+                const E irt = tdiv((E)1, rt);
                 const float ux = (float)(fma((E)0.5, Fsx, (E)jx) * irt);
                 const float uy = (float)(fma((E)0.5, Fsy, (E)jy) * irt);
                 const float u2 = ux * ux + uy * uy;

@@ -108,6 +108,15 @@ template <> struct PV<float> {
 // which is the printed equation regrouped (the two p's cancel, so it holds
 // for p <= 0 too).  Every operation is in the arithmetic type E.
 // ---------------------------------------------------------------------------
+// Quotient and logarithm in the arithmetic type of a kernel: binary64 uses
+// the correctly rounded operations; binary32 thermodynamics use the
+// hardware approximations __fdividef (2 ulp) and __logf (absolute error
+// 2^-21.41 on [0.5, 2], 3 ulp elsewhere).
+__device__ __forceinline__ double tdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float tdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double tlog(double x) { return log(x); }
+__device__ __forceinline__ float tlog(float x) { return __logf(x); }
+
 template <int NC, typename E = double>
 __device__ __forceinline__ void pr_lnf(const Params &P, const E (&rm)[NC], E (&lnf)[NC], E *p_out)
 {
@@ -116,7 +125,7 @@ __device__ __forceinline__ void pr_lnf(const Params &P, const E (&rm)[NC], E (&l
     E rho = 0;
 #pragma unroll
     for (int i = 0; i < NC; ++i) rho += rm[i];
-    const E inv = (E)1 / rho;
+    const E inv = tdiv((E)1, rho);
     E x[NC];
 #pragma unroll
     for (int i = 0; i < NC; ++i) x[i] = rm[i] * inv;
@@ -138,15 +147,15 @@ __device__ __forceinline__ void pr_lnf(const Params &P, const E (&rm)[NC], E (&l
     const E B = bm * rho;
     const E omB = (E)1 - B;
     const E den = fma(B, (E)2 - B, (E)1);  // 1 + 2B - B^2
-    const E amr = am * rho / RT;
-    const E Zm1 = B / omB - amr / den;
-    const E Lr = log(fma((E)1 + kSqrt2, B, (E)1) / fma((E)1 - kSqrt2, B, (E)1));
-    const E C0 = V::lnRT(P) - log(omB);
-    const E invbm = (E)1 / bm;
-    const E C1 = Zm1 * invbm + am * Lr * invbm * invbm / ((E)2 * kSqrt2 * RT);
-    const E C2 = -Lr * invbm / (kSqrt2 * RT);
+    const E amr = tdiv(am * rho, RT);
+    const E Zm1 = tdiv(B, omB) - tdiv(amr, den);
+    const E Lr = tlog(tdiv(fma((E)1 + kSqrt2, B, (E)1), fma((E)1 - kSqrt2, B, (E)1)));
+    const E C0 = V::lnRT(P) - tlog(omB);
+    const E invbm = tdiv((E)1, bm);
+    const E C1 = Zm1 * invbm + tdiv(am * Lr * invbm * invbm, (E)2 * kSqrt2 * RT);
+    const E C2 = tdiv(-Lr * invbm, kSqrt2 * RT);
 #pragma unroll
-    for (int i = 0; i < NC; ++i) lnf[i] = log(rm[i]) + C0 + fma(V::b(P, i), C1, S[i] * C2);
+    for (int i = 0; i < NC; ++i) lnf[i] = tlog(rm[i]) + C0 + fma(V::b(P, i), C1, S[i] * C2);
     if (p_out) *p_out = RT * rho / omB - am * rho * rho / den;
 }
 

@@ -329,10 +329,12 @@ __global__ void __launch_bounds__(kT)
     }
 }
 
+// Shared rows of the binary32 kernel have a fixed pitch of kT entries (a strip
+// needs at most W + 6 <= kT), so every row offset is a compile-time constant.
 template <int NC, typename E> struct Smem32 {
-    static __host__ __device__ constexpr size_t rs(int W) { return align16((size_t)4 * NC * (W + 6) * sizeof(float)); }
-    static __host__ __device__ constexpr size_t ps(int W) { return align16((size_t)3 * (W + 6) * sizeof(E)); }
-    static __host__ __device__ constexpr size_t mu(int W) { return align16((size_t)3 * NC * (W + 4) * sizeof(E)); }
+    static __host__ __device__ constexpr size_t rs(int) { return align16((size_t)4 * NC * kT * sizeof(float)); }
+    static __host__ __device__ constexpr size_t ps(int) { return align16((size_t)3 * kT * sizeof(E)); }
+    static __host__ __device__ constexpr size_t mu(int) { return align16((size_t)3 * NC * kT * sizeof(E)); }
     static __host__ __device__ constexpr size_t xc() { return align16((size_t)6 * NC * kT * sizeof(float)); }
     static __host__ __device__ constexpr size_t red() { return align16((size_t)(kT / 32) * NC * sizeof(double)); }
     static __host__ __device__ constexpr size_t ms() { return align16((size_t)2 * NC * kT * sizeof(float)); }
@@ -365,10 +367,10 @@ __global__ void __launch_bounds__(kT)
     using V = PV<E>;
     using SM = Smem32<NC, E>;
     extern __shared__ __align__(16) unsigned char smem[];
-    float *RS = (float *)smem;                                   // [4][NC][W+6] rho hi rows
-    float *RL = (float *)(smem + SM::rs(W));                     // [4][NC][W+6] rho lo rows
-    E *PS = (E *)(smem + 2 * SM::rs(W));                         // [3][W+6]     psi rows
-    E *MU = (E *)(smem + 2 * SM::rs(W) + SM::ps(W));             // [3][NC][W+4] mu rows
+    float *RS = (float *)smem;                                   // [4][NC][kT] rho hi rows
+    float *RL = (float *)(smem + SM::rs(W));                     // [4][NC][kT] rho lo rows
+    E *PS = (E *)(smem + 2 * SM::rs(W));                         // [3][kT]     psi rows
+    E *MU = (E *)(smem + 2 * SM::rs(W) + SM::ps(W));             // [3][NC][kT] mu rows
     float *XC = (float *)(smem + 2 * SM::rs(W) + SM::ps(W) + SM::mu(W));  // [6][NC][kT] exchange
     double *RED = (double *)((unsigned char *)XC + SM::xc());
     float *MS = (float *)((unsigned char *)RED + SM::red());     // [2][NC][kT] mass of rows written
@@ -379,7 +381,7 @@ __global__ void __launch_bounds__(kT)
 
     const int nx = P.nx, ny = P.ny;
     const IDX N = (IDX)P.N;
-    const int CW = W + 6, CM = W + 4;
+    constexpr int CW = kT, CM = kT;  // row pitch (columns used: W + 6 and W + 4)
     const int x0 = blockIdx.x * W;
     const int w = min(W, nx - x0);
     const int y0 = blockIdx.y * H;
@@ -458,18 +460,20 @@ __global__ void __launch_bounds__(kT)
                     MU[((q % 3) * NC + i) * CM + c + 2] = fma(RT, lf[i], -V::sqk(P, i) * lap);
             }
         }
-        if (kk + 1 < nrows) {
-            const IDX rowb = (IDX)wrapc(k + 1, ny) * (IDX)nx;
+        __syncthreads();
+        // density pair of row k+1 for phase (A) of the next row: issued here
+        // before the first collision row, in the density update after it
+        const IDX rowb1 = (IDX)wrapc(k + 1, ny) * (IDX)nx + (IDX)xA0;
+        if (kk < 4) {
+            if (kk + 1 < nrows && hasA0) {
 #pragma unroll
-            for (int i = 0; i < NC; ++i) {
-                if (hasA0) {
-                    rh0[i] = __ldg(rhin + i * N + rowb + xA0);
-                    rl0[i] = __ldg(rlin + i * N + rowb + xA0);
+                for (int i = 0; i < NC; ++i) {
+                    rh0[i] = __ldg(rhin + i * N + rowb1);
+                    rl0[i] = __ldg(rlin + i * N + rowb1);
                 }
             }
+            continue;
         }
-        __syncthreads();
-        if (kk < 4) continue;
         // ---- (C) collision of row k-2 (moving populations only) --------------------
         const int q = kk - 2;
         const bool own_row = crow >= y0 && crow < y0 + h;
@@ -523,19 +527,24 @@ __global__ void __launch_bounds__(kT)
                 Fx[i] = (float)fx;
                 Fy[i] = (float)fy;
             }
-            const E irt = (E)1 / rt;
+            const E irt = tdiv((E)1, rt);
             const float ux = (float)(fma((E)0.5, Fsx, (E)jx) * irt);
             const float uy = (float)(fma((E)0.5, Fsy, (E)jy) * irt);
             const float u2 = ux * ux + uy * uy;
-            // per-direction constants of Eqs. (1a)-(1c):
-            //   g* = (1-w) g + rho (w w_a B_a) + cF w_a [Fe (3 + 9 ue) + 3 ue Ge + K_class]
-            float WB[9], C9[9], U3[9];
+            // Eqs. (1a)-(1c) over the four pairs of opposite directions (a, a+1):
+            //   g*_a = (1 - w) g_a + sym +- anti,
+            //   sym  = rho_i WBs + cw [3ue (3Fe + Ge) + K],  anti = rho_i WBa + 3 cw Fe,
+            // WBs = w w_a (4.5 ue^2 - 1.5 u^2), WBa = 3 w w_a ue, cw = (1 - w/2) w_a,
+            // ue = e_a.u, Fe = e_a.F_i, Ge = e_a.grad rho_i, K the class term
+            float WBs[4], WBa[4], U3[4];
 #pragma unroll
-            for (int a = 1; a < 9; ++a) {
+            for (int p = 0; p < 4; ++p) {
+                const int a = 2 * p + 1;
                 const float ue = (float)L::e(a, 0) * ux + (float)L::e(a, 1) * uy;
-                WB[a] = om * (float)L::w(a) * (ue * fmaf(4.5f, ue, 3.0f) - 1.5f * u2);
-                C9[a] = fmaf(9.0f, ue, 3.0f);
-                U3[a] = 3.0f * ue;
+                const float ow = om * (float)L::w(a);
+                WBs[p] = ow * fmaf(4.5f * ue, ue, -1.5f * u2);
+                WBa[p] = (3.0f * ow) * ue;
+                U3[p] = 3.0f * ue;
             }
 #pragma unroll
             for (int i = 0; i < NC; ++i) {
@@ -549,31 +558,49 @@ __global__ void __launch_bounds__(kT)
                 const float ri = r1[cc] + rlo1[i];
                 const float Fu3 = 3.0f * (Fx[i] * ux + Fy[i] * uy);
                 const float Gu = Gx * ux + Gy * uy;
-                // cW = (3 e^2 - D)/2 - 1 with D = 2: faces -1/2, diagonals +1
+                // class term: faces -Gu/2 - 3F.u, diagonals Gu - 3F.u
                 const float Kf = fmaf(-0.5f, Gu, -Fu3), Kd = Gu - Fu3;
                 const float *v = hv[i] - 1;  // v[a], a = 1..8
                 float d = 0.0f;
 #pragma unroll
-                for (int a = 1; a < 9; ++a) {
+                for (int p = 0; p < 4; ++p) {
+                    const int a = 2 * p + 1;  // e_{a+1} = -e_a
                     const int ex = L::e(a, 0), ey = L::e(a, 1);
                     const float cw = cF * (float)L::w(a);
                     const float Fe = (float)ex * Fx[i] + (float)ey * Fy[i];
                     const float Ge = (float)ex * Gx + (float)ey * Gy;
-                    const float Fa = fmaf(Fe, C9[a], fmaf(U3[a], Ge, (ex != 0 && ey != 0) ? Kd : Kf));
-                    const float gs = fmaf(om1, v[a], fmaf(ri, WB[a], cw * Fa));
-                    if (interior && own_row) gout[(i * 8 + a - 1) * N + dst[a]] = gs;
-                    d += gs;
-                    if (ex == 0) {
-                        if (ey < 0) own0[i] = gs;
-                        else own2[i] = gs;
-                    } else {
-                        XC[(((ey + 1) * 2 + (ex > 0 ? 0 : 1)) * NC + i) * kT + t] = gs;
+                    const float S = fmaf(U3[p], fmaf(3.0f, Fe, Ge), (ex != 0 && ey != 0) ? Kd : Kf);
+                    const float sym = fmaf(ri, WBs[p], cw * S);
+                    const float anti = fmaf(ri, WBa[p], (3.0f * cw) * Fe);
+                    const float gp = fmaf(om1, v[a], sym + anti);
+                    const float gm = fmaf(om1, v[a + 1], sym - anti);
+                    d += gp;
+                    d += gm;
+#pragma unroll
+                    for (int sgn = 0; sgn < 2; ++sgn) {
+                        const int b = a + sgn;
+                        const float gs = sgn ? gm : gp;
+                        const int bx = L::e(b, 0), by = L::e(b, 1);
+                        if (interior && own_row) gout[(i * 8 + b - 1) * N + dst[b]] = gs;
+                        if (bx == 0) {
+                            if (by < 0) own0[i] = gs;
+                            else own2[i] = gs;
+                        } else {
+                            XC[(((by + 1) * 2 + (bx > 0 ? 0 : 1)) * NC + i) * kT + t] = gs;
+                        }
                     }
                 }
                 dep[i] = d;
             }
         }
         __syncthreads();
+        if (kk + 1 < nrows && hasA0) {
+#pragma unroll
+            for (int i = 0; i < NC; ++i) {
+                rh0[i] = __ldg(rhin + i * N + rowb1);
+                rl0[i] = __ldg(rlin + i * N + rowb1);
+            }
+        }
         // ---- density update of the interior columns ---------------------------------
         if (interior) {
             const bool write_row = (crow - 1) >= y0 && (crow - 1) < y0 + h;
