@@ -10,10 +10,11 @@
 //   P1  psi = sum_j sqrt(kappa_j) rho~_j at every node
 //   P2  ln f_i and mu_i = RT ln f_i - sqrt(kappa_i) lap psi at every node
 //   P3  F_i = -rho~_i grad mu_i, grad rho_i, u, equilibrium, forcing and BGK of
-//       the moving populations, pushed to the other buffer; the node's
-//       departures are kept in shared memory
-//   P4  new densities: old - departures + the populations that arrived (read
-//       back from the other buffer), all by Fast2Sum into the pairs
+//       the moving populations, pushed to the other buffer; each departure
+//       leaves the node's density pair by its own Fast2Sum (the hi part goes
+//       to DEP, the lo part stays in RL, which no other node reads in P3)
+//   P4  new densities: that pair plus the populations that arrived (read back
+//       from the other buffer), by Fast2Sum
 // State format is the binary32 one of the single-problem path (Q-1 moving
 // populations and an exact density pair), so a job's result does not depend
 // on the other jobs, on which CTA runs it, or on the CTA size.
@@ -235,7 +236,7 @@ __global__ void k_batch_round(const Shared S, const Job *__restrict__ jobs, Stat
                     const float Fu3 = 3.0f * (Fx[i] * ux + Fy[i] * uy);
                     const float Gu = Gx * ux + Gy * uy;
                     const float Kf = fmaf(-0.5f, Gu, -Fu3), Kd = Gu - Fu3;
-                    float d = 0.0f;
+                    float dh = RH[i * N + n], dl = RL[i * N + n];
 #pragma unroll
                     for (int a = 1; a < 9; ++a) {
                         const int ex = L::e(a, 0), ey = L::e(a, 1);
@@ -245,9 +246,10 @@ __global__ void k_batch_round(const Shared S, const Job *__restrict__ jobs, Stat
                         const float Fa = fmaf(Fe, C9[a], fmaf(U3[a], Ge, (ex != 0 && ey != 0) ? Kd : Kf));
                         const float gs = fmaf(om1, hv[i][a - 1], fmaf(ri[i], WB[a], cw * Fa));
                         gout[(long long)(i * 8 + a - 1) * N + dst[a]] = gs;
-                        d += gs;
+                        pair_acc_b(dh, dl, -gs);
                     }
-                    DEP[i * N + n] = d;
+                    DEP[i * N + n] = dh;
+                    RL[i * N + n] = dl;
                 }
             }
             __syncthreads();
@@ -255,8 +257,7 @@ __global__ void k_batch_round(const Shared S, const Job *__restrict__ jobs, Stat
             for (int n = t; n < N; n += T) {
 #pragma unroll
                 for (int i = 0; i < NC; ++i) {
-                    float hi = RH[i * N + n], lo = RL[i * N + n];
-                    pair_acc_b(hi, lo, -DEP[i * N + n]);
+                    float hi = DEP[i * N + n], lo = RL[i * N + n];
 #pragma unroll
                     for (int a = 0; a < 8; ++a) pair_acc_b(hi, lo, gout[(long long)(i * 8 + a) * N + n]);
                     const float h2 = hi + lo;

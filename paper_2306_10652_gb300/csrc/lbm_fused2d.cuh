@@ -479,7 +479,6 @@ __global__ void __launch_bounds__(kT)
         const bool own_row = crow >= y0 && crow < y0 + h;
         const int yc = wrapc(crow, ny);
         float own0[NC], own2[NC];  // dx = 0 moving values, dy = -1 and +1
-        float dep[NC];             // sum of this node's departures
         if (active) {
             const IDX yd[3] = {(IDX)wrapc(yc - 1, ny) * (IDX)nx, (IDX)yc * (IDX)nx,
                                (IDX)wrapc(yc + 1, ny) * (IDX)nx};
@@ -561,7 +560,6 @@ __global__ void __launch_bounds__(kT)
                 // class term: faces -Gu/2 - 3F.u, diagonals Gu - 3F.u
                 const float Kf = fmaf(-0.5f, Gu, -Fu3), Kd = Gu - Fu3;
                 const float *v = hv[i] - 1;  // v[a], a = 1..8
-                float d = 0.0f;
 #pragma unroll
                 for (int p = 0; p < 4; ++p) {
                     const int a = 2 * p + 1;  // e_{a+1} = -e_a
@@ -574,8 +572,9 @@ __global__ void __launch_bounds__(kT)
                     const float anti = fmaf(ri, WBa[p], (3.0f * cw) * Fe);
                     const float gp = fmaf(om1, v[a], sym + anti);
                     const float gm = fmaf(om1, v[a + 1], sym - anti);
-                    d += gp;
-                    d += gm;
+                    // each departure leaves the pair of row crow (bH, bL) by its own Fast2Sum
+                    pair_acc(bH[i], bL[i], -gp);
+                    pair_acc(bH[i], bL[i], -gm);
 #pragma unroll
                     for (int sgn = 0; sgn < 2; ++sgn) {
                         const int b = a + sgn;
@@ -590,7 +589,6 @@ __global__ void __launch_bounds__(kT)
                         }
                     }
                 }
-                dep[i] = d;
             }
         }
         __syncthreads();
@@ -624,10 +622,9 @@ __global__ void __launch_bounds__(kT)
                     MS[(0 * NC + i) * kT + t] = ms;
                     MS[(1 * NC + i) * kT + t] = mc + lo;
                 }
-                // row crow: its departures, then arrivals along the row
+                // row crow (its departures left during the collision): arrivals along the row
                 aH[i] = bH[i];
                 aL[i] = bL[i];
-                pair_acc(aH[i], aL[i], -dep[i]);
                 pair_acc(aH[i], aL[i], xc[2 * NC * kT + t - 1]);
                 pair_acc(aH[i], aL[i], xc[3 * NC * kT + t + 1]);
                 // row crow+1: its old density, then the first arrivals
