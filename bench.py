@@ -51,10 +51,10 @@ def initial_density(d, case, nx, ny, seed=2):
 
 # DRAM bytes per node-step of the fused binary32 step at Nc = 10, from the ncu
 # capture summarised in profiles/fused32_fp32_spinodal2048_nc10.md (2048 x 512
-# case: dram read + write = 836.1 MB over 1,048,576 nodes).  The traffic is
+# case: dram read + write = 836.6 MB over 1,048,576 nodes).  The traffic is
 # per node (strip/segment halos come from L2), so it scales with the nodes of
 # a launch.  None for any other form or Nc, or once the kernel changes.
-NCU_TRAFFIC_B_PER_NODE = {("fp32", "auto", 10): (460.14336e6 + 375.950336e6) / 1048576}
+NCU_TRAFFIC_B_PER_NODE = {("fp32", "auto", 10): (460.083712e6 + 376.51712e6) / 1048576}
 
 
 def traffic_per_launch(args, nc, N):
