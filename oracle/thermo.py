@@ -238,6 +238,80 @@ def flash(P: OracleProblem, p, z, tol=1e-12, maxit=10000, K0=None):
 
 
 # ---------------------------------------------------------------------------
+# Multiphase PT flash (three-phase case of Sec. 3.4), textbook successive
+# substitution: K-values of every phase against a reference phase, phase
+# fractions from the multiphase Rachford-Rice equations, ln phi of each phase
+# from its own cubic root.
+# ---------------------------------------------------------------------------
+def rachford_rice_multi(z, K, beta0):
+    """Phase fractions beta[k] of the non-reference phases, K[k, i] = x_{k,i} / x_{ref,i}:
+    the roots of g_k = sum_i z_i (K_{k,i} - 1) / t_i, t_i = 1 + sum_m beta_m (K_{m,i} - 1)
+    (the reference phase takes 1 - sum beta).  Newton's method with step halving that
+    keeps every t_i positive; None if it does not converge."""
+    beta = np.array(beta0, float)
+    D = K - 1.0
+    for _ in range(200):
+        t = 1.0 + beta @ D
+        g = D @ (z / t)
+        H = -(D * (z / t ** 2)) @ D.T
+        try:
+            step = np.linalg.solve(H, g)
+        except np.linalg.LinAlgError:
+            return None
+        lam = 1.0
+        while lam > 1e-12:
+            nb = beta - lam * step
+            if np.all(1.0 + nb @ D > 0.0):
+                break
+            lam *= 0.5
+        beta = nb
+        if np.max(np.abs(lam * step)) < 1e-15:
+            break
+    t = 1.0 + beta @ D
+    if np.max(np.abs(D @ (z / t))) > 1e-12:
+        return None
+    return beta
+
+
+def flash3(P: OracleProblem, p, z, guesses, phases, tol=1e-12, maxit=20000):
+    """Multiphase split of overall composition z at (T, p) by successive
+    substitution.  guesses: starting compositions of the phases; phases: their
+    cubic roots ('V' largest Z, 'L' smallest Z).  The last phase is the
+    reference.  Returns a FlashResult with beta (mole fraction of each phase),
+    x (compositions), rho (total molar densities), rhoi (per component), S
+    (volume fractions), iterations and the final max |ln f_{k,i} - ln f_{ref,i}|;
+    None if a phase vanishes or the iteration does not converge."""
+    z = np.asarray(z, float)
+    z = z / z.sum()
+    n = len(phases)
+    x = [np.asarray(g, float) / np.sum(g) for g in guesses]
+    beta = np.full(n - 1, 1.0 / n)
+    for it in range(1, maxit + 1):
+        st = [phase_state(P, p, x[k], phases[k]) for k in range(n)]
+        lnphi = np.array([s[1] for s in st])
+        lnf = lnphi + np.log(np.array(x) * p)
+        err = float(np.max(np.abs(lnf[:-1] - lnf[-1])))
+        if err < tol:
+            break
+        K = np.exp(lnphi[-1] - lnphi[:-1])  # x_k / x_ref
+        beta = rachford_rice_multi(z, K, beta)
+        if beta is None:
+            return None
+        xr = z / (1.0 + beta @ (K - 1.0))
+        x = [K[k] * xr for k in range(n - 1)] + [xr]
+        x = [xi / xi.sum() for xi in x]
+    else:
+        return None
+    b = np.append(beta, 1.0 - beta.sum())
+    if np.any(b <= 0.0):
+        return None
+    rho = np.array([s[0] for s in st])
+    v = b / rho
+    return FlashResult(beta=b, x=np.array(x), rho=rho, rhoi=np.array(x) * rho[:, None], S=v / v.sum(),
+                       iterations=it, residual=err)
+
+
+# ---------------------------------------------------------------------------
 # spinodal test: d ln f_i / d rho~_j
 # ---------------------------------------------------------------------------
 def hessian_lnf(P: OracleProblem, rho_molar, rel_step=1e-6):

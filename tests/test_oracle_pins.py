@@ -11,7 +11,7 @@ import pytest
 
 import np_lbm
 from oracle import OracleProblem, feq_forcing, lattice_info
-from oracle.thermo import LatticeUnits, flash, maxwell
+from oracle.thermo import LatticeUnits, flash, flash3, maxwell, phase_state
 from oracle.workloads import slab, two_phase_pressure
 from paper_2306_10652_gb300 import synth
 
@@ -371,3 +371,92 @@ def test_flat_interface_binary_reaches_flash():
     assert np.max(np.abs(xL / f2.x - 1)) < 5e-3 and np.max(np.abs(xV / f2.y - 1)) < 5e-3
     # iso-fugacity between the phase centres (same sublattice: x = 0 and nx/2)
     assert np.max(np.abs(m["lnf"][:, 0, 0, nx // 2] - m["lnf"][:, 0, 0, 0])) < 5e-5
+
+
+# ---------------------------------------------------------------------------
+# three-phase flash (Sec. 3.4)
+# ---------------------------------------------------------------------------
+def three_phase_case():
+    comp, err = [], {}
+    for line in open(f"{GOLDEN}/three_phase.txt"):
+        if line.startswith("#") or not line.strip():
+            continue
+        f = line.split()
+        if f[0] == "ERR":
+            err[f[1]] = np.array([float(v) for v in f[2:]])
+        else:
+            comp.append((f[0], float(f[1]), float(f[2]), float(f[3]), float(f[4]), float(f[5]), float(f[6])))
+    names = [c[0] for c in comp]
+    lu = LatticeUnits([c[2] for c in comp], [c[1] for c in comp], [c[3] for c in comp], [c[4] for c in comp],
+                      ref=names.index("C1"), a_ref=0.011550, b_ref=0.107781)
+    d = [c[6] for c in comp]
+    k = np.zeros((3, 3))
+    k[0, :] = d
+    k[:, 0] = d
+    z = np.array([c[5] for c in comp])
+    return names, lu, k, z, err
+
+
+def three_phase_flash(P, p, z, fl2):
+    """V, liquid1 (C4-rich), liquid2 (CO2-rich) from the two-phase vapour and
+    two liquid guesses on either side of the two-phase liquid."""
+    return flash3(P, p, z, [fl2.y, np.array([0.5, 0.01, 0.49]), np.array([0.95, 0.02, 0.03])], ["V", "L", "L"])
+
+
+def test_three_phase_flash_reproduces_stated_saturations():
+    """At 225 K, 9 bar the paper states vapour, liquid1, liquid2 volume
+    fractions of 0.25, 0.5, 0.25 (printed to two digits) and orders the
+    liquids by density."""
+    names, lu, k, z, _ = three_phase_case()
+    P = lu.problem(225.0, kij=k)
+    p = lu.p(9.0)
+    fl2 = flash(P, p, z)
+    r = three_phase_flash(P, p, z, fl2)
+    assert r is not None and r.residual < 1e-12
+    assert np.abs(r.S - np.array([0.25, 0.5, 0.25])).max() < 5e-3, r.S
+    assert r.rho[0] < r.rho[1] < r.rho[2]
+    # material balance and one pressure (each phase's root reproduces p through Eq. 9)
+    assert np.abs(r.beta @ r.x - z / z.sum()).max() < 1e-12
+    for k_ in range(3):
+        assert abs(P.eos(r.rhoi[k_])[0] / p - 1.0) < 1e-10
+
+
+def test_three_phase_split_lowers_gibbs_energy():
+    """The three-phase split has lower Gibbs energy (sum_k n_k sum_i x_ki ln f_ki,
+    per mole, at the same T and p) than the two-phase split of the same z,
+    which is therefore not the stable state."""
+    names, lu, k, z, _ = three_phase_case()
+    P = lu.problem(225.0, kij=k)
+    p = lu.p(9.0)
+    fl2 = flash(P, p, z)
+    r = three_phase_flash(P, p, z, fl2)
+
+    def g(beta, xs, kinds):
+        tot = 0.0
+        for b, x, kind in zip(beta, xs, kinds):
+            _, lnphi = phase_state(P, p, x, kind)
+            tot += b * float(x @ (lnphi + np.log(x * p)))
+        return tot
+
+    g2 = g([fl2.beta, 1.0 - fl2.beta], [fl2.y, fl2.x], ["V", "L"])
+    g3 = g(r.beta, r.x, ["V", "L", "L"])
+    assert g3 < g2 - 1e-6, (g3, g2)
+
+
+def test_multiphase_rachford_rice_reduces_to_two_phases():
+    """With two phases, flash3 (Newton on the multiphase Rachford-Rice
+    equations) reproduces the two-phase flash (bracketed scalar Rachford-Rice)."""
+    P = synthetic_problem(3, 3, Tfac=0.8)
+    z = np.array([0.5, 0.3, 0.2])
+    pmid = None
+    for pt in np.geomspace(1e-4, 1.0, 200):
+        f = flash(P, pt, z)
+        if f is not None and 0.3 < f.beta < 0.7:
+            pmid = pt
+            break
+    assert pmid is not None
+    f2 = flash(P, pmid, z)
+    r = flash3(P, pmid, z, [f2.y * 0.9 + 0.1 * z, f2.x * 0.9 + 0.1 * z], ["V", "L"])
+    assert r is not None
+    assert abs(r.beta[0] - f2.beta) < 1e-9
+    assert np.abs(r.x[0] - f2.y).max() < 1e-9 and np.abs(r.x[1] - f2.x).max() < 1e-9
