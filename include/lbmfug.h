@@ -196,8 +196,9 @@ int lbm_destroy(lbm_problem *p);
  * non-finite value was seen, else 0.  Returns LBM_EINVAL for NULL pointers,
  * n < 1, or nc outside 1..LBM_MAX_NC (the scratch capacity).  The first call
  * on a device looks up the scratch address and should come before any
- * stream capture.  Calls share the scratch: calls that can overlap on the
- * GPU race.
+ * stream capture; the address is looked up again after the device's context
+ * was rebuilt (for example by cudaDeviceReset).  Calls share the scratch:
+ * calls that can overlap on the GPU race.
  */
 int lbm_field_sums_noalloc(const double *d_field, int nc, long long n, double *d_out,
                            int *d_nonfinite, void *stream);

@@ -259,11 +259,15 @@ def rachford_rice_multi(z, K, beta0):
         except np.linalg.LinAlgError:
             return None
         lam = 1.0
+        feasible = False
         while lam > 1e-12:
             nb = beta - lam * step
             if np.all(1.0 + nb @ D > 0.0):
+                feasible = True
                 break
             lam *= 0.5
+        if not feasible:  # no step keeps every t_i > 0: the split is not found
+            return None
         beta = nb
         if np.max(np.abs(lam * step)) < 1e-15:
             break

@@ -11,10 +11,10 @@ liquid1 | vapour | liquid1 | liquid2 | liquid1, phase centres at nx/4 (vapour),
 nx/2 (liquid1) and 3 nx/4 (liquid2).
 
 Checks after 1e7 steps (the paper's count): the three phases persist, with
-molar densities within 0.5 % and mole fractions within 2 % of the initial
+molar densities within 0.1 % and mole fractions within 1.5 % of the initial
 three-phase flash; the component fugacities of the three bulk phases agree
 within 1 % (iso-fugacity); the bulk pressures (Eq. 9 at the phase centres)
-agree within 5 %.
+agree within 4 %.
 
 What is not reproduced: the paper compares with the flash at the LBM's
 pressure and finds at most 0.273 %.  Here the bulk pressures stay about 3 %
@@ -122,18 +122,33 @@ def errors(lu, P, r):
 
 
 def test_three_phase_state():
+    """Tolerances are about twice the recorded results (densities within
+    0.05 % of the initial flash, mole fractions within 1 %, fugacity ratios
+    within 0.5 %, bulk pressures 3 % apart), so a tenfold regression of the
+    kernel on this case fails.  The comparison the paper makes (the flash at
+    the LBM's own pressure and composition) is printed beside the paper's
+    error table; its gap is the recorded quasi-stationary pressure spread, so
+    it is reported, not asserted."""
     names, lu, P, out = run()
     r = out[-1]
-    _, _, k, z, _, _ = case()
+    _, _, k, z, _, paper_err = case()
     r0 = split(P, lu.p(P_BAR), z)
     lnf, pr = [], []
     for kk, ph in enumerate(r["phases"]):
         assert np.isfinite(ph).all()
-        assert abs(ph.sum() / r0.rho[kk] - 1.0) <= 5e-3, (kk, ph.sum(), r0.rho[kk])
-        assert np.abs((ph / ph.sum()) / r0.x[kk] - 1.0).max() <= 2e-2, (kk, ph / ph.sum(), r0.x[kk])
+        assert abs(ph.sum() / r0.rho[kk] - 1.0) <= 1e-3, (kk, ph.sum(), r0.rho[kk])
+        assert np.abs((ph / ph.sum()) / r0.x[kk] - 1.0).max() <= 1.5e-2, (kk, ph / ph.sum(), r0.x[kk])
         p_k, lnf_k = P.eos(ph)
         pr.append(p_k)
         lnf.append(lnf_k)
     lnf = np.array(lnf)
     assert np.abs(np.exp(lnf[1:] - lnf[0]) - 1.0).max() <= 1e-2, np.exp(lnf[1:] - lnf[0])
-    assert (max(pr) - min(pr)) / min(pr) <= 5e-2, pr
+    assert (max(pr) - min(pr)) / min(pr) <= 4e-2, pr
+    try:
+        errs = errors(lu, P, r)
+    except AssertionError:
+        errs = None
+    for ph in ("V", "L1", "L2"):
+        ours = "no split" if errs is None else \
+            "rho %.4f %%, x %s %%" % (100 * errs[ph][0], np.round(100 * errs[ph][1], 4).tolist())
+        print(f"three-phase {ph}: this run {ours}; paper {paper_err.get(ph)}")

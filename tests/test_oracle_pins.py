@@ -136,6 +136,42 @@ def test_alpha_is_one_at_critical_temperature():
         assert abs(P.alpha()[0] - 1.0) < 1e-14
 
 
+@pytest.mark.parametrize("omega,tol", [(0.0, 4e-3), (0.2, 4e-3), (0.4, 4e-3),
+                                       (0.4901, 2e-4), (0.55, 2e-4), (0.7, 2e-4), (0.85, 2e-4),
+                                       (1.0, 2e-4), (1.2, 2e-4)])
+def test_alpha_reproduces_the_acentric_factor(omega, tol):
+    """Both branches of alpha_i (Sec. 2.3) against the definition of the
+    acentric factor, omega = -log10(p_sat / p_c) - 1 at T_r = 0.7: the PR
+    temperature function was regressed so that the EOS returns that vapour
+    pressure.  The oracle's Maxwell construction (pinned to Case 1 of the
+    paper elsewhere) at 0.7 Tc must give back omega; the omega > 0.49 branch
+    does so within 1e-4 over (0.49, 1.2], the omega <= 0.49 branch within
+    3.3e-3.  A wrong sign, a dropped term or a transposed digit in the
+    leading coefficients of either branch moves the recovered omega by more
+    than these tolerances."""
+    import math
+    a, b = 2.0 / 49.0, 2.0 / 21.0
+    Tc = OracleProblem(0, 1, 1, 1, [a], [b], [omega], T=1.0).critical_temperatures()[0]
+    P = OracleProblem(0, 1, 1, 1, [a], [b], [omega], T=0.7 * Tc)
+    psat = maxwell(P)[0]
+    pc = 0.077796074 * P.R * Tc / b  # b = Omega_b R Tc / pc (Sec. 2.3)
+    assert abs((-math.log10(psat / pc) - 1.0) - omega) < tol
+
+
+def test_alpha_branches_meet_at_omega_049():
+    """The two branches of alpha_i are one correlation split at omega = 0.49:
+    at the split their m(omega) differ by 0.40 %, and alpha at T_r = 0.5 by
+    less than 0.5 %.  The first branch is taken at exactly 0.49 (the
+    inequality is <= in Sec. 2.3)."""
+    a, b = 2.0 / 49.0, 2.0 / 21.0
+    Tc = OracleProblem(0, 1, 1, 1, [a], [b], [0.49], T=1.0).critical_temperatures()[0]
+    vals = [OracleProblem(0, 1, 1, 1, [a], [b], [om], T=0.5 * Tc).alpha()[0]
+            for om in (0.49 - 1e-9, 0.49, 0.49 + 1e-9)]
+    assert vals[0] == pytest.approx(vals[1], rel=1e-8)           # <= 0.49: first branch
+    jump = vals[2] / vals[1] - 1.0
+    assert 1e-3 < jump < 5e-3                                    # the second branch above
+
+
 def test_printed_eq12_matches_where_p_positive():
     """The oracle's cancelled form equals Eq. (12) as printed wherever p > 0."""
     P = synthetic_problem(11, 4, shape=(1, 1, 1), Tfac=1.5)
