@@ -54,7 +54,7 @@ def initial_density(d, case, nx, ny, seed=2):
 # case: dram read + write = 836.6 MB over 1,048,576 nodes).  The traffic is
 # per node (strip/segment halos come from L2), so it scales with the nodes of
 # a launch.  None for any other form or Nc, or once the kernel changes.
-NCU_TRAFFIC_B_PER_NODE = {("fp32", "auto", 10): (460.083712e6 + 376.51712e6) / 1048576}
+NCU_TRAFFIC_B_PER_NODE = {}
 
 
 def traffic_per_launch(args, nc, N):
@@ -210,7 +210,8 @@ def run_gpu(args):
     forms = None
     if not args.no_forms:
         forms = {}
-        for name, pr, sc, k in (("fp32dev_fused", lbmfug.LBM_FP32DEV, lbmfug.LBM_SCHED_AUTO, 6),
+        for name, pr, sc, k in (("fp32dev_fused", lbmfug.LBM_FP32DEV, lbmfug.LBM_SCHED_AUTO, 10),
+                                ("fp32_fused", lbmfug.LBM_FP32, lbmfug.LBM_SCHED_AUTO, 10),
                                 ("fp64_fused", lbmfug.LBM_FP64, lbmfug.LBM_SCHED_AUTO, 4),
                                 ("fp64_threepass", lbmfug.LBM_FP64, lbmfug.LBM_SCHED_THREEPASS, 4)):
             if pr == prec and sc == sched:
@@ -295,26 +296,91 @@ def run_e2e(args, lbmfug, case, rho, nx, ny, prec, sched, local):
             "wall_s": wall}
 
 
-def oracle_sample(case, nx, ny, rho, crop=64, steps=4):
-    """Time the CPU oracle on a crop of the workload (bounded sample)."""
+def cpu_info():
+    """(logical cores, CPU model) of the host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return os.cpu_count() or 1, model or "unknown"
+
+
+def oracle_rate(case, rho, crop, steps, threads):
+    """Nc*GLUPS of the CPU oracle on a crop x crop piece of the workload."""
     from oracle import OracleProblem
+    from oracle.orc import set_threads
     nc = case["nc"]
+    used = set_threads(threads)
     P = OracleProblem(0, crop, crop, 1, case["a"], case["b"], case["omega"], np.asarray(case["kij"]),
                       T=case["T"], tau=case["tau"], kappa_ref=case["kappa_ref"])
-    g = P.init_equilibrium(np.ascontiguousarray(rho[:, :, :crop, :crop]))
+    g = P.init_equilibrium(np.ascontiguousarray(rho[:nc, :, :crop, :crop]))
     t0 = time.perf_counter()
     P.step(g, steps)
     dt = time.perf_counter() - t0
-    return nc * crop * crop * steps / dt / 1e9, dt
+    return nc * crop * crop * steps / dt / 1e9, dt, used
 
 
-def cpu_baseline(case, nx, ny, rho, target_s=12.0):
-    crop, steps = 64, 2
-    v, dt = oracle_sample(case, nx, ny, rho, crop, steps)
-    steps = max(2, min(400, int(steps * target_s / max(dt, 1e-3))))
-    v, dt = oracle_sample(case, nx, ny, rho, crop, steps)
-    return {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": f"{crop}x{crop} crop of the workload, {steps} steps ({dt:.1f} s), single thread"}
+def config0_rate():
+    """The binary flat-interface configuration in full (D2Q9 128 x 4, Nc = 2,
+    binary64, tau = 1, 5000 steps) on the oracle: Nc*GLUPS, seconds."""
+    from oracle.orc import set_threads
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from helpers import oracle_problem, seeded_mixture
+    from oracle.workloads import slab, two_phase_pressure
+    from paper_2306_10652_gb300 import synth
+    nx, ny, nc = 128, 4, 2
+    c = seeded_mixture(0, nc, 0, (1, ny, nx))
+    orc = oracle_problem(c, 0, (1, ny, nx))
+    _, fl = two_phase_pressure(orc, np.ones(nc) / nc, 0.5)
+    rho = np.repeat(slab(fl.rhoi_V, fl.rhoi_L, nx)[:, None, None, :], ny, axis=2)
+    rho = rho * synth.multiplicative_noise(0, rho.shape, 1e-3)
+    set_threads(1)  # 512 nodes: below the oracle's parallel threshold
+    g = orc.init_equilibrium(rho)
+    t0 = time.perf_counter()
+    orc.step(g, 5000)
+    dt = time.perf_counter() - t0
+    return nc * nx * ny * 5000 / dt / 1e9, dt
+
+
+def cpu_baseline(case, nx, ny, rho, crop=256):
+    """The oracle on the host cores (a reported baseline, not the target):
+    the workload on a 256 x 256 crop single-threaded and on every core, the
+    same crop for Nc = 1..10, and the binary flat-interface configuration in
+    full.  About 20-30 s of CPU work."""
+    ncores, model = cpu_info()
+    v1, dt1, _ = oracle_rate(case, rho, crop, 1, 1)
+    vN, dtN, used = oracle_rate(case, rho, crop, 2, 0)
+    per_nc = {}
+    d = json.load(open(WORKLOAD_FILE))
+    for nc in range(1, 11):
+        cs = [c for c in d["cases"] if c["nc"] == nc][0]
+        r = initial_density(d, cs, crop, crop)
+        a, _, _ = oracle_rate(cs, r, crop, 1, 1)
+        b, _, _ = oracle_rate(cs, r, crop, 2, 0)
+        per_nc[nc] = {"single_thread": a * 1e3, "all_cores": b * 1e3}
+    c0, dt0 = config0_rate()
+    from oracle.orc import set_threads
+    set_threads(0)
+    return {"value": vN, "unit": METRIC, "cores": used, "kind": "oracle",
+            "sample": f"{crop}x{crop} crop of the workload, 2 steps on {used} threads ({dtN:.1f} s)",
+            "single_thread": {"value": v1, "sample": f"same crop, 1 step ({dt1:.1f} s)"},
+            "host": {"nproc": ncores, "cpu_model": model},
+            "per_nc_mlups_256crop": per_nc,
+            "config0_full": {"value_nc_mlups": c0 * 1e3, "seconds": dt0,
+                             "workload": "binary flat interface D2Q9 128x4, Nc=2, 5000 steps, one thread"}}
 
 
 TERNARY_FILE = os.path.join(ROOT, "paper_2306_10652_gb300", "workloads", "ternary_sweep.json")
@@ -335,19 +401,77 @@ def ternary_jobs(limit=None):
     return d, jobs
 
 
+def ulp32(x):
+    """Spacing of binary32 numbers at x > 0."""
+    return 2.0 ** (np.floor(np.log2(np.float32(x))) - 23)
+
+
+def tie_line_errors(d, jobs, states, sample):
+    """Largest relative deviation of each sampled converged slab's vapour and
+    liquid mole fractions (x = 0 and x = nx/2) from the oracle flash at the
+    slab's own pressure (Eq. 9 at the two centres) and conserved composition."""
+    from oracle import OracleProblem
+    from oracle.thermo import flash
+    errs = []
+    for k in sample:
+        T, rho = jobs[k]
+        st = states[k]
+        if not st["converged"]:
+            continue
+        P = OracleProblem(0, 1, 1, 1, d["a"], d["b"], d["omega"], np.asarray(d["kij"]), T=T,
+                          kappa_ref=d["kappa_ref"])
+        rm = st["rho"][:, 0]
+        nx = rm.shape[1]
+        rV, rL = rm[:, 0], rm[:, nx // 2]
+        p = 0.5 * (P.eos(rV)[0] + P.eos(rL)[0])
+        tot = rm.sum(axis=1)
+        fl = flash(P, p, tot / tot.sum())
+        if fl is None:
+            continue
+        errs.append(max(np.abs((rV / rV.sum()) / fl.y - 1).max(), np.abs((rL / rL.sum()) / fl.x - 1).max()))
+    return errs
+
+
+def fp64_one_at_a_time(lbmfug, d, jobs, order, tol, every, cap, budget_s):
+    """The plain binary64 per-problem path, one slab after the other, each run
+    to the same criterion as the batched form (largest density change per
+    `every` steps below max(tol, 8 ulp of binary32 at its largest density)),
+    until budget_s has passed.  Returns (solves, seconds, node-steps)."""
+    t0 = time.perf_counter()
+    solved, node_steps = 0, 0
+    for k in order:
+        if time.perf_counter() - t0 > budget_s:
+            break
+        T, rho = jobs[k]
+        bar = max(tol, 8 * ulp32(1.05 * rho.max()))
+        p = lbmfug.Problem(0, rho.shape[2], rho.shape[1], 1, d["a"], d["b"], d["omega"], np.asarray(d["kij"]),
+                           T, d["tau"], precision=lbmfug.LBM_FP64, kappa_ref=d["kappa_ref"])
+        p.init_fields(rho[:, None])
+        p.convergence()
+        steps = 0
+        while steps < cap:
+            p.step(every)
+            steps += every
+            if p.convergence() < bar:
+                solved += 1
+                break
+        node_steps += steps * rho.shape[1] * rho.shape[2]
+        p.close()
+    return solved, time.perf_counter() - t0, node_steps
+
+
 def run_batched(args, lbmfug, local):
-    """Batched form: all sweep slabs to convergence (solves/s), and the plain
-    binary64 per-problem path timed on a sample of the same slabs."""
-    import torch
+    """Batched form: all sweep slabs to convergence (solves/s) with the tie-line
+    error of a sample against the oracle flash, and the plain binary64
+    per-problem path measured on a sample of the same slabs to the same
+    criterion."""
     d, jobs = ternary_jobs(args.batch_jobs)
-    # binary32 storage jitters at the resolution of its populations: converged
-    # = largest density change below 2e-6 per 1000 steps (~8 ulp at rho ~ 2)
     tol, every, cap = 2e-6, 1000, args.batch_max_steps
     t0 = time.perf_counter()
     with lbmfug.Batch(d["a"], d["b"], d["omega"], np.asarray(d["kij"]), d["tau"], jobs,
                       precision=lbmfug.LBM_FP32, kappa_ref=d["kappa_ref"]) as bt:
         t1 = time.perf_counter()
-        done = bt.run(cap, every, tol)
+        bt.run(cap, every, tol)
         t2 = time.perf_counter()
         states = [bt.state(k) for k in range(len(jobs))]
         info = bt.info()
@@ -355,32 +479,23 @@ def run_batched(args, lbmfug, local):
     failed = sum(s["failed"] for s in states)
     node_steps = sum(s["steps"] * r.shape[1] * r.shape[2] for s, (_, r) in zip(states, jobs))
     wall = t2 - t1
-    # binary64 single-problem path, one problem at a time, on a sample of the slabs
-    sample = sorted(range(len(jobs)), key=lambda k: jobs[k][1].shape[2])[:: max(1, len(jobs) // 6)]
-    fp64_ms = {}
-    for k in sample:
-        T, rho = jobs[k]
-        p = lbmfug.Problem(0, rho.shape[2], rho.shape[1], 1, d["a"], d["b"], d["omega"], np.asarray(d["kij"]),
-                           T, d["tau"], precision=lbmfug.LBM_FP64, kappa_ref=d["kappa_ref"])
-        p.init_fields(rho[:, None])
-        p.step(200)
-        p.synchronize()
-        e0 = time.perf_counter()
-        p.step(2000)
-        p.synchronize()
-        fp64_ms[rho.shape[2]] = (time.perf_counter() - e0) / 2000 * 1e3
-        p.close()
-    sizes = sorted(fp64_ms)
-    est_fp64 = 0.0
-    for s, (_, r) in zip(states, jobs):
-        if s["converged"]:
-            est_fp64 += s["steps"] * float(np.interp(r.shape[2], sizes, [fp64_ms[v] for v in sizes])) * 1e-3
-    return {"jobs": len(jobs), "converged": conv, "failed": failed, "criterion": f"max|drho| < {tol} per {every} steps",
+    rng = np.random.default_rng(5)
+    sample = rng.permutation(len(jobs))
+    errs = tie_line_errors(d, jobs, states, sample[:48])
+    s64, w64, ns64 = fp64_one_at_a_time(lbmfug, d, jobs, sample, tol, every, cap, args.batch_fp64_s)
+    unconv = [k for k, s in enumerate(states) if not s["converged"] and not s["failed"]]
+    return {"jobs": len(jobs), "converged": conv, "failed": failed,
+            "criterion": f"max|drho| per {every} steps < max({tol}, 8 ulp_binary32(largest density))",
             "max_steps": cap, "wall_s": wall, "setup_s": t1 - t0, "solves_per_s": conv / wall,
             "node_steps_per_s": node_steps / wall, "threads": info["threads"], "ctas": info["ctas"],
-            "rounds": info["rounds"], "precision": "fp32",
-            "fp64_per_problem": {"ms_per_step_by_nx": fp64_ms,
-                                 "estimated_solves_per_s": conv / est_fp64 if est_fp64 > 0 else None}}
+            "rounds": info["rounds"], "precision": "fp32 (binary32 state and thermodynamics)",
+            "unconverged_last_drho": sorted(float(states[k]["last_drho"]) for k in unconv)[-5:],
+            "tie_line_vs_flash": {"slabs": len(errs), "max_rel": float(max(errs)) if errs else None,
+                                  "median_rel": float(np.median(errs)) if errs else None},
+            "fp64_one_at_a_time": {"measured": True, "solves": s64, "wall_s": w64,
+                                   "solves_per_s": s64 / w64 if w64 > 0 else None,
+                                   "node_steps_per_s": ns64 / w64 if w64 > 0 else None,
+                                   "sample": "slabs of the sweep in a seeded random order, each to the criterion"}}
 
 
 SERVE_FILE = os.path.join(ROOT, "paper_2306_10652_gb300", "workloads", "served_requests.json")
@@ -402,10 +517,11 @@ def served_field(r, W):
 
 
 def run_served(args, lbmfug):
-    """Served form: the requests arrive with their Poisson gaps, run to
-    convergence under the 80 % memory budget; latency percentiles, solves/s,
-    and the plain binary64 path run one request at a time (estimated from
-    its measured per-step time for every request)."""
+    """Served form: the requests arrive with their Poisson gaps and run to
+    convergence under the 80 % memory budget; latency percentiles and solves/s
+    count converged requests only.  The plain binary64 path is measured on the
+    same requests one at a time, each to the same criterion, for a bounded
+    time."""
     d = json.load(open(SERVE_FILE))
     reqs = d["requests"]
     tol, every, cap = 2e-6, 1000, args.serve_max_steps
@@ -422,61 +538,78 @@ def run_served(args, lbmfug):
         t1 = time.perf_counter()
         polls = [srv.poll(j) for j in ids]
         stats = srv.stats()
-    lat = np.array([p["latency_s"] for p in polls])
-    done = [p for p in polls if p["state"] in ("converged", "exhausted")]
-    conv = sum(p["state"] == "converged" for p in polls)
+    conv = [p for p in polls if p["state"] == "converged"]
+    lat = np.array([p["latency_s"] for p in conv]) if conv else np.array([np.nan])
     work = sum(p["steps"] * r["nc"] * r["nx"] * r["ny"] * r["nz"] for p, r in zip(polls, reqs))
-    # binary64 per-request path: each request alone, per-step time measured on 20 steps
-    est = 0.0
-    for p, r, rho in zip(polls, reqs, fields):
+    # binary64, one request at a time, each to the same criterion, for a bounded time
+    order = np.random.default_rng(6).permutation(len(reqs))
+    b0 = time.perf_counter()
+    solved64 = 0
+    for k in order:
+        if time.perf_counter() - b0 > args.serve_fp64_s:
+            break
+        r, rho = reqs[k], fields[k]
+        bar = max(tol, 8 * ulp32(1.05 * rho.max()))
         prob = lbmfug.Problem(r["lattice"], r["nx"], r["ny"], r["nz"], r["a"], r["b"], r["omega"],
                               np.asarray(r["kij"]), r["T"], d["tau"], precision=lbmfug.LBM_FP64,
                               kappa_ref=d["kappa_ref"])
         prob.init_fields(rho)
-        prob.step(5)
-        prob.synchronize()
-        e0 = time.perf_counter()
-        prob.step(20)
-        prob.synchronize()
-        est += (time.perf_counter() - e0) / 20 * p["steps"]
+        prob.convergence()
+        steps = 0
+        while steps < cap:
+            prob.step(every)
+            steps += every
+            if prob.convergence() < bar:
+                solved64 += 1
+                break
         prob.close()
-    return {"requests": len(reqs), "converged": conv, "finished": len(done),
+    w64 = time.perf_counter() - b0
+    return {"requests": len(reqs), "converged": len(conv),
+            "exhausted": sum(p["state"] == "exhausted" for p in polls),
             "failed": sum(p["state"] == "failed" for p in polls),
-            "criterion": f"max|drho| < {tol} per {every} steps, cap {cap} steps",
+            "criterion": f"max|drho| per {every} steps < max({tol}, 8 ulp_binary32(1.05 x largest density)), "
+                         f"cap {cap} steps",
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-            "wall_s": t1 - t0, "solves_per_s": len(done) / (t1 - t0),
+            "latency_over": "converged requests",
+            "wall_s": t1 - t0, "solves_per_s": len(conv) / (t1 - t0),
             "nc_node_steps_per_s": work / (t1 - t0), "slots": args.serve_slots,
             "peak_bytes": stats["peak_bytes"], "budget_bytes": stats["budget_bytes"], "rounds": stats["rounds"],
-            "precision": "fp32dev (binary32 populations, binary64 EOS and forces)",
-            "fp64_one_at_a_time": {"estimated_wall_s": est, "estimated_solves_per_s": len(done) / est if est else None}}
+            "precision": "fp32dev (binary32 populations; thermodynamics double-binary32 on D2Q9, binary64 on D3Q19)",
+            "fp64_one_at_a_time": {"measured": True, "solves": solved64, "wall_s": w64,
+                                   "solves_per_s": solved64 / w64 if w64 > 0 else None,
+                                   "sample": "requests in a seeded random order, each alone to the criterion"}}
 
 
 def run_reference(args):
+    """The oracle as the reference arm: each bench step a bounded sample of the
+    workload (a 256 x 256 crop, all host cores), on rank 0 only."""
     ws, rank, _ = dist_setup()
     if rank != 0:
         return None
     d, case = load_case(args.nc)
     nx, ny = d["nx"], d["ny"]
-    rho = initial_density(d, case, 64, 64)
-    crop = 64
+    crop = 256
+    rho = initial_density(d, case, crop, crop)
+    ncores, model = cpu_info()
     for _ in range(args.warmup):
-        oracle_sample(case, nx, ny, rho, crop, 1)
+        oracle_rate(case, rho, crop, 1, 0)
+    _, dt1, used = oracle_rate(case, rho, crop, 1, 0)
     per_step_s = max(0.5, 60.0 / max(args.steps, 1))
-    _, dt1 = oracle_sample(case, nx, ny, rho, crop, 1)
     inner = max(1, int(per_step_s / max(dt1, 1e-3)))
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle_sample(case, nx, ny, rho, crop, inner)
+        oracle_rate(case, rho, crop, inner, 0)
     wall = time.perf_counter() - t0
     nc = case["nc"]
     value = nc * crop * crop * inner * args.steps / wall / 1e9
-    sample = f"{crop}x{crop} crop of the workload, {inner} oracle steps per bench step, single thread"
+    sample = f"{crop}x{crop} crop of the workload, {inner} oracle steps per bench step, {used} threads"
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": f"spinodal decomposition D2Q9 {nx}x{ny} periodic, Nc={nc}",
                                             "lattice": "D2Q9", "nx": nx, "ny": ny, "nc": nc},
-            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": used, "kind": "oracle", "sample": sample,
+                             "host": {"nproc": ncores, "cpu_model": model}},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -487,16 +620,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--nc", type=int, default=10)
-    ap.add_argument("--precision", default="fp32", choices=["fp32dev", "fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32dev", choices=["fp32dev", "fp32", "fp64"])
     ap.add_argument("--no-forms", action="store_true", help="skip the comparison forms")
     ap.add_argument("--grid", default=None, help="NXxNY override of the workload grid (profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-jobs", type=int, default=None, help="first N jobs of the sweep")
     ap.add_argument("--batch-max-steps", type=int, default=400000)
+    ap.add_argument("--batch-fp64-s", type=float, default=60.0, help="seconds of the binary64 one-at-a-time sample")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--serve-slots", type=int, default=8)
-    ap.add_argument("--serve-max-steps", type=int, default=20000)
+    ap.add_argument("--serve-max-steps", type=int, default=200000)
+    ap.add_argument("--serve-fp64-s", type=float, default=60.0, help="seconds of the binary64 one-at-a-time sample")
     ap.add_argument("--schedule", default="auto", choices=["auto", "threepass", "fused"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -53,7 +53,12 @@ enum lbm_lattice { LBM_D2Q9 = 0, LBM_D3Q19 = 1 };
  *               compensated sums of the populations that left and arrived
  *               (component mass conserved to the rounding of the pair);
  *               collision in binary32; Peng-Robinson mixture, fugacities,
- *               forces and mass sums in binary64.
+ *               chemical-potential differences of the force and mass sums at
+ *               binary64 accuracy: the fused schedule evaluates them in
+ *               double-binary32 arithmetic (pairs hi + lo of binary32 values
+ *               with error-free sums and products, relative error about
+ *               2^-44) on the binary32 units, which GB300 runs at 64 times
+ *               its binary64 rate; the three-pass schedule uses binary64.
  *  LBM_FP32:    the LBM_FP32DEV storage, with the thermodynamics and forces of
  *               the fused schedule in binary32 too (the three-pass schedule
  *               keeps them in binary64). */
@@ -142,6 +147,31 @@ int lbm_moments(lbm_problem *p, double *rho, double *u, double *pressure, double
 /* Same into device buffers, enqueued on the handle's stream. */
 int lbm_moments_device(lbm_problem *p, double *d_rho, double *d_u, double *d_pressure,
                        double *d_lnf);
+
+/*
+ * Chemical potentials and interaction forces of the current state, D2Q9
+ * only, into caller-owned host buffers (either may be NULL, not both):
+ * F[i][d][y][x] = -rho~_i (grad mu_i)_d and mu[i][y][x] = RT ln f_i -
+ * sqrt(kappa_i) lap psi, the force of Eq. (5) with kappa_ij =
+ * sqrt(kappa_i kappa_j) (Eq. 4), psi = sum_j sqrt(kappa_j) rho~_j and the
+ * isotropic lattice stencils for grad and lap.  They are evaluated with the
+ * arithmetic the step uses: binary64 (LBM_FP64, or the three-pass
+ * schedule), double-binary32 (LBM_FP32DEV fused: mu carried as a pair,
+ * every difference of the gradient taken on the pairs and rounded once, F
+ * in binary32) or binary32 (LBM_FP32 fused).  LBM_ENOTSUP for D3Q19.
+ * Synchronises.
+ */
+int lbm_forces(lbm_problem *p, double *F, double *mu);
+
+/*
+ * Launch geometry of the handle's step (valid after lbm_init_fields):
+ * *fused = 1 for the single-pass D2Q9 kernel, 0 for the three-pass
+ * schedule; for the fused kernel, the interior columns per CTA (*strip),
+ * CTAs along x (*nstrips), rows per CTA (*seg_h) and CTAs along y (*segs).
+ * Any pointer may be NULL.
+ */
+int lbm_schedule_info(const lbm_problem *p, int *fused, int *strip, int *nstrips, int *seg_h,
+                      int *segs);
 
 /*
  * Per-component total mass sum_r rho_i(r) into mass[Nc] (host), summed in a
@@ -233,8 +263,11 @@ int lbm_batch_create(lbm_batch **out, int Nc, const double *a, const double *b, 
 
 /* Run rounds of check_every steps until every problem has finished or
  * max_steps steps have been taken.  A problem finishes when the largest
- * change of its densities over a round is below tol (converged) or when a
- * density is not finite (failed; it is retired and the others go on).
+ * change of its densities over a round is below max(tol, 8 ulp) (converged),
+ * ulp being the spacing of binary32 numbers at the problem's largest
+ * density (the stored populations are binary32, and below that their
+ * rounding, not relaxation, moves the densities), or when a density is not
+ * finite (failed; it is retired and the others go on).
  * *n_converged receives the number of finished problems.  Synchronises. */
 int lbm_batch_run(lbm_batch *b, long long max_steps, int check_every, double tol, int *n_converged);
 
@@ -262,7 +295,9 @@ int lbm_batch_destroy(lbm_batch *b);
  * than max_active jobs run; every running job is its own problem on its own
  * stream, advanced in rounds of check_every steps whose kernels overlap on
  * the GPU; a job finishes when the largest density change over a round is
- * below tol (converged), when a density is not finite (failed) or after
+ * below tol (converged; with binary32 storage below max(tol, 8 ulp of
+ * binary32 at 1.05 times its largest initial density)), when a density is
+ * not finite (failed) or after
  * max_steps steps (exhausted), and its memory goes to the next request.
  * ------------------------------------------------------------------------ */
 typedef struct lbm_request {

@@ -26,12 +26,22 @@
  * Population state convention: g[i][alpha][node] holds the post-streaming
  * (pre-collision) populations g_{alpha,i}(r, t) of Eq. (1a), node index
  * x + nx*(y + ny*z), x fastest.
+ *
+ * Loops over nodes whose iterations are independent carry OpenMP pragmas
+ * (built with -fopenmp; orc_set_threads picks the thread count).  Every
+ * value is computed by one thread with the same operations in the same
+ * order as serially, so results do not depend on the thread count; the one
+ * reduction (orc_mass) stays serial.
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
 #define ORC_MAXNC 16
+#define ORC_PAR_MIN 4096 /* nodes below which the loops run on one thread */
 #define ORC_MAXQ 19
 
 /* ------------------------------------------------------------------ */
@@ -275,6 +285,7 @@ static void orc_gradient_L(const orc_problem *P, const orc_lattice *L, const dou
                            double *G /*[D][N]*/)
 {
     const long N = (long)P->nx * P->ny * P->nz;
+#pragma omp parallel for collapse(2) schedule(static) if ((long)P->nx * P->ny * P->nz >= ORC_PAR_MIN)
     for (int z = 0; z < P->nz; ++z)
         for (int y = 0; y < P->ny; ++y)
             for (int x = 0; x < P->nx; ++x) {
@@ -291,6 +302,7 @@ static void orc_gradient_L(const orc_problem *P, const orc_lattice *L, const dou
 static void orc_laplacian_L(const orc_problem *P, const orc_lattice *L, const double *X,
                             double *Y)
 {
+#pragma omp parallel for collapse(2) schedule(static) if ((long)P->nx * P->ny * P->nz >= ORC_PAR_MIN)
     for (int z = 0; z < P->nz; ++z)
         for (int y = 0; y < P->ny; ++y)
             for (int x = 0; x < P->nx; ++x) {
@@ -377,6 +389,7 @@ static int orc_macroscopic(const orc_problem *P, const orc_lattice *L, const dou
 
     /* densities: rho_i = sum_a g_{a,i}; rho~_i = rho_i / M_i */
     for (int i = 0; i < nc; ++i)
+#pragma omp parallel for schedule(static) if (N >= ORC_PAR_MIN)
         for (long r = 0; r < N; ++r) {
             double s = 0.0;
             for (int a = 0; a < Q; ++a) s += g[((long)i * Q + a) * N + r];
@@ -384,13 +397,19 @@ static int orc_macroscopic(const orc_problem *P, const orc_lattice *L, const dou
             f->rhom[(long)i * N + r] = s / P->M[i];
         }
     /* Eq. (9), Eq. (12) node by node */
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad) if (N >= ORC_PAR_MIN)
     for (long r = 0; r < N; ++r) {
         double rm[ORC_MAXNC], lf[ORC_MAXNC], p;
         for (int i = 0; i < nc; ++i) rm[i] = f->rhom[(long)i * N + r];
-        if (orc_eos(P, rm, &p, lf) != 0) return -2;
+        if (orc_eos(P, rm, &p, lf) != 0) {
+            bad = 1;
+            continue;
+        }
         f->p[r] = p;
         for (int i = 0; i < nc; ++i) f->lnf[(long)i * N + r] = lf[i];
     }
+    if (bad) return -2;
     /* Eq. (5): F_i = -rho~_i RT grad ln f_i + rho~_i sum_j grad(sqrt(k_i k_j) lap rho~_j) */
     double *lap = f->scratch;               /* [nc][N] lap rho~_j */
     double *Phi = f->scratch + (long)nc * N; /* [N] */
@@ -398,6 +417,7 @@ static int orc_macroscopic(const orc_problem *P, const orc_lattice *L, const dou
     for (int j = 0; j < nc; ++j) orc_laplacian_L(P, L, f->rhom + (long)j * N, lap + (long)j * N);
     for (int i = 0; i < nc; ++i) {
         /* interface part: Phi_i = sum_j sqrt(kappa_i kappa_j) lap rho~_j */
+#pragma omp parallel for schedule(static) if (N >= ORC_PAR_MIN)
         for (long r = 0; r < N; ++r) {
             double s = 0.0;
             for (int j = 0; j < nc; ++j) s += sqrt(kappa[i] * kappa[j]) * lap[(long)j * N + r];
@@ -405,17 +425,20 @@ static int orc_macroscopic(const orc_problem *P, const orc_lattice *L, const dou
         }
         orc_gradient_L(P, L, Phi, G);
         for (int d = 0; d < D; ++d)
+#pragma omp parallel for schedule(static) if (N >= ORC_PAR_MIN)
             for (long r = 0; r < N; ++r)
                 f->F[((long)i * D + d) * N + r] = f->rhom[(long)i * N + r] * G[(long)d * N + r];
         /* bulk part: -rho~_i RT grad ln f_i */
         orc_gradient_L(P, L, f->lnf + (long)i * N, G);
         for (int d = 0; d < D; ++d)
+#pragma omp parallel for schedule(static) if (N >= ORC_PAR_MIN)
             for (long r = 0; r < N; ++r)
                 f->F[((long)i * D + d) * N + r] += -f->rhom[(long)i * N + r] * RT * G[(long)d * N + r];
         /* grad rho_i for the forcing term, Eq. (1c) */
         orc_gradient_L(P, L, f->rho + (long)i * N, f->gradrho + (long)i * D * N);
     }
     /* barycentric velocity with the half-force shift */
+#pragma omp parallel for schedule(static) if (N >= ORC_PAR_MIN)
     for (long r = 0; r < N; ++r) {
         double rho_tot = 0.0;
         for (int i = 0; i < nc; ++i) rho_tot += f->rho[(long)i * N + r];
@@ -457,6 +480,7 @@ int orc_step(const orc_problem *P, const double *g_in, double *g_out, long long 
         status = orc_macroscopic(P, &L, g, &f);
         if (status) break;
         /* collision, Eq. (1a) right-hand side */
+#pragma omp parallel for schedule(static) if (N >= ORC_PAR_MIN)
         for (long r = 0; r < N; ++r) {
             double u[3] = {0, 0, 0};
             for (int d = 0; d < D; ++d) u[d] = f.u[(long)d * N + r];
@@ -474,7 +498,8 @@ int orc_step(const orc_problem *P, const double *g_in, double *g_out, long long 
                 }
             }
         }
-        /* streaming, Eq. (1a) left-hand side */
+        /* streaming, Eq. (1a) left-hand side (a permutation: no two nodes write one place) */
+#pragma omp parallel for collapse(2) schedule(static) if ((long)P->nx * P->ny * P->nz >= ORC_PAR_MIN)
         for (int z = 0; z < P->nz; ++z)
             for (int y = 0; y < P->ny; ++y)
                 for (int x = 0; x < P->nx; ++x) {
@@ -536,6 +561,19 @@ int orc_init_equilibrium(const orc_problem *P, const double *rho, const double *
             for (int a = 0; a < Q; ++a) g[((long)i * Q + a) * N + r] = geq[a];
         }
     return 0;
+}
+
+/* Threads of the OpenMP loops (n < 1: all the runtime offers); returns the
+ * count in use, 1 without OpenMP. */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n < 1 ? omp_get_num_procs() : n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 /* Per-component total mass sum_r rho_i(r). */

@@ -29,7 +29,7 @@ def build_oracle(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -58,6 +58,8 @@ def _load():
             lib.orc_critical_temperature.restype = ctypes.c_double
             lib.orc_feq_forcing.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, _dp, _dp, _dp]
             lib.orc_lattice_info.argtypes = [ctypes.c_int, _ip, _ip, _ip, _dp]
+            lib.orc_set_threads.argtypes = [ctypes.c_int]
+            lib.orc_set_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -67,6 +69,12 @@ def _ptr(a: np.ndarray | None):
         return None
     assert a.dtype == np.float64 and a.flags.c_contiguous
     return a.ctypes.data_as(_dp)
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's node loops (n < 1: every core); returns the count in use.
+    Results do not depend on it."""
+    return int(_load().orc_set_threads(int(n)))
 
 
 def lattice_info(lattice: int):

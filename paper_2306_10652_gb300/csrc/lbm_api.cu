@@ -10,6 +10,7 @@
 #include <new>
 #include <vector>
 
+#include "lbm_df64.cuh"
 #include "lbm_internal.h"
 #include "lbmfug.h"
 
@@ -36,6 +37,7 @@ struct lbm_problem {
     ThreePassWork w{};
     double *snap = nullptr;
     bool have_snap = false;
+    void *fscratch = nullptr;  // psi / mu scratch of lbm_forces
     long long launches = 0;
     long long monitor_step = -1;
     double *mon = nullptr;  // [nc] latest monitored mass
@@ -99,6 +101,13 @@ double pr_alpha(double a, double b, double omega, double T, double R)
     return s * s;
 }
 
+float2 split2(double x)
+{
+    const float h = (float)x;
+    return make_float2(h, (float)(x - (double)h));
+}
+
+// binary64 constants -> the binary32 and double-binary32 copies
 void refresh_float_params(Params &P)
 {
     P.fRT = (float)P.RT;
@@ -110,6 +119,21 @@ void refresh_float_params(Params &P)
         P.frhobar[i] = (float)P.rhobar[i];
     }
     for (int k = 0; k < kMaxNc * kMaxNc; ++k) P.fA[k] = (float)P.A[k];
+    for (int i = 0; i < kMaxNc; ++i) {
+        const double invM = P.invM[i] > 0.0 ? P.invM[i] : 1.0;
+        P.dM[i] = split2(invM);
+        P.dB[i] = split2(P.b[i] * invM);
+        P.db[i] = split2(P.b[i]);
+        P.dRK[i] = split2(P.RT * (P.lnRT + std::log(invM)));
+        P.dsqk[i] = split2(P.sqk[i]);
+        P.dPk[i] = split2(P.sqk[i] * invM);
+        for (int j = 0; j < kMaxNc; ++j) {
+            const double invMj = P.invM[j] > 0.0 ? P.invM[j] : 1.0;
+            P.dA[i * kMaxNc + j] = split2(P.A[i * kMaxNc + j] * invMj);
+        }
+    }
+    P.dRT = split2(P.RT);
+    df::make_log_table(&P.logtab[0].x);
 }
 
 void build_params(lbm_problem *p)
@@ -429,6 +453,59 @@ int lbm_moments(lbm_problem *p, double *rho, double *u, double *pressure, double
     cudaFree(d_u);
     cudaFree(d_p);
     return st;
+}
+
+int lbm_forces(lbm_problem *p, double *F, double *mu)
+{
+    if (!p || (!F && !mu)) return LBM_EINVAL;
+    if (!p->initialized) return LBM_ESTATE;
+    if (p->sticky) return p->sticky;
+    if (p->lattice != LBM_D2Q9) return LBM_ENOTSUP;
+    // the arithmetic of the step: the fused schedule's thermodynamics form, or
+    // binary64 for the three-pass schedule and for binary64 storage
+    const int prec = (!p->fused || p->opt.precision == LBM_FP64) ? 0 : (p->opt.precision == LBM_FP32DEV ? 1 : 2);
+    const size_t N = (size_t)p->N, nc = (size_t)p->nc;
+    if (!p->fscratch) {
+        p->fscratch = dev_alloc(p, (nc + 1) * N * sizeof(double));
+        if (!p->fscratch) return LBM_ENOMEM;
+    }
+    double *dF = nullptr, *dmu = nullptr;
+    if (cudaMalloc(&dF, nc * 2 * N * sizeof(double)) != cudaSuccess) return LBM_ENOMEM;
+    if (mu && cudaMalloc(&dmu, nc * N * sizeof(double)) != cudaSuccess) {
+        cudaFree(dF);
+        return LBM_ENOMEM;
+    }
+    int st = LBM_OK;
+    if (launch_fields(p->lattice, sprec(p), p->nc, p->P, p->st[p->cur], p->w, p->w.rho, nullptr, nullptr,
+                      nullptr, p->stream))
+        st = LBM_ECUDA;
+    p->launches += 1;
+    if (!st) {
+        const int e = p->nc <= 8 ? launch_forces_lo(prec, p->nc, p->P, p->w.rho, p->fscratch, dF, dmu, p->stream)
+                                 : launch_forces_hi(prec, p->nc, p->P, p->w.rho, p->fscratch, dF, dmu, p->stream);
+        p->launches += 3;
+        if (e) st = LBM_ECUDA;
+    }
+    if (!st && F && cudaMemcpyAsync(F, dF, nc * 2 * N * sizeof(double), cudaMemcpyDeviceToHost, p->stream))
+        st = LBM_ECUDA;
+    if (!st && mu && cudaMemcpyAsync(mu, dmu, nc * N * sizeof(double), cudaMemcpyDeviceToHost, p->stream))
+        st = LBM_ECUDA;
+    if (!st && cudaStreamSynchronize(p->stream) != cudaSuccess) st = LBM_ECUDA;
+    cudaFree(dF);
+    cudaFree(dmu);
+    return st;
+}
+
+int lbm_schedule_info(const lbm_problem *p, int *fused, int *strip, int *nstrips, int *seg_h, int *segs)
+{
+    if (!p) return LBM_EINVAL;
+    if (!p->allocated) return LBM_ESTATE;
+    if (fused) *fused = p->fused ? 1 : 0;
+    if (strip) *strip = p->fused ? p->geo.strip : 0;
+    if (nstrips) *nstrips = p->fused ? p->geo.nstrips : 0;
+    if (seg_h) *seg_h = p->fused ? p->geo.seg_h : 0;
+    if (segs) *segs = p->fused ? p->geo.segs : 0;
+    return LBM_OK;
 }
 
 int lbm_mass(lbm_problem *p, double *mass)

@@ -66,6 +66,12 @@ __device__ __forceinline__ int wrapb(int v, int n)
     return v < 0 ? v + n : v;
 }
 
+// unit in the last place of a positive normal binary32 number
+__device__ __forceinline__ double ulp32(float x)
+{
+    return ldexp(1.0, ((__float_as_int(x) >> 23) & 0xff) - 127 - 23);
+}
+
 __device__ __forceinline__ void pair_acc_b(float &hi, float &lo, float x)
 {
     const float s = hi + x;
@@ -73,45 +79,16 @@ __device__ __forceinline__ void pair_acc_b(float &hi, float &lo, float x)
     hi = s;
 }
 
-// thermodynamics of one node at the job's temperature (binary32 or binary64)
-template <int NC, typename E>
-__device__ __forceinline__ void job_lnf(const Shared &S, const Job &J, const E (&rm)[NC], E (&lnf)[NC])
-{
-    const E kSqrt2 = (E)1.4142135623730951;
-    E rho = 0;
-#pragma unroll
-    for (int i = 0; i < NC; ++i) rho += rm[i];
-    const E inv = tdiv((E)1, rho);
-    E x[NC];
-#pragma unroll
-    for (int i = 0; i < NC; ++i) x[i] = rm[i] * inv;
-    E bm = 0;
-#pragma unroll
-    for (int i = 0; i < NC; ++i) bm = fma(x[i], (E)S.b[i], bm);
-    E Sv[NC];
-#pragma unroll
-    for (int i = 0; i < NC; ++i) {
-        E s = 0;
-#pragma unroll
-        for (int j = 0; j < NC; ++j) s = fma((E)J.A[i * kMaxNcBatch + j], x[j], s);
-        Sv[i] = s;
-    }
-    E am = 0;
-#pragma unroll
-    for (int i = 0; i < NC; ++i) am = fma(x[i], Sv[i], am);
-    const E RT = (E)J.RT;
-    const E B = bm * rho;
-    const E omB = (E)1 - B;
-    const E den = fma(B, (E)2 - B, (E)1);
-    const E Zm1 = tdiv(B, omB) - tdiv(tdiv(am * rho, RT), den);
-    const E Lr = tlog(tdiv(fma((E)1 + kSqrt2, B, (E)1), fma((E)1 - kSqrt2, B, (E)1)));
-    const E C0 = (E)J.lnRT - tlog(omB);
-    const E invbm = tdiv((E)1, bm);
-    const E C1 = Zm1 * invbm + tdiv(am * Lr * invbm * invbm, (E)2 * kSqrt2 * RT);
-    const E C2 = tdiv(-Lr * invbm, kSqrt2 * RT);
-#pragma unroll
-    for (int i = 0; i < NC; ++i) lnf[i] = tlog(rm[i]) + C0 + fma((E)S.b[i], C1, Sv[i] * C2);
-}
+// Constants of Eqs. (9)-(12) for one job: the shared b_i and the job's own
+// temperature (pr_lnf_v of lbm_core.cuh evaluates the equations).
+template <typename E> struct JobView {
+    const Shared &S;
+    const Job &J;
+    __device__ E A(int i, int j) const { return (E)J.A[i * kMaxNcBatch + j]; }
+    __device__ E b(int i) const { return (E)S.b[i]; }
+    __device__ E RT() const { return (E)J.RT; }
+    __device__ E lnRT() const { return (E)J.lnRT; }
+};
 
 template <int NC, typename E>
 __global__ void k_batch_round(const Shared S, const Job *__restrict__ jobs, Status *__restrict__ status,
@@ -123,6 +100,7 @@ __global__ void k_batch_round(const Shared S, const Job *__restrict__ jobs, Stat
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_job;
     __shared__ float s_red[32];
+    __shared__ float s_rmax[32];
     const int t = threadIdx.x, T = blockDim.x;
     const float om = (float)S.omega, om1 = (float)(1.0 - S.omega), cF = (float)(1.0 - 0.5 * S.omega);
     for (;;) {
@@ -168,7 +146,7 @@ __global__ void k_batch_round(const Shared S, const Job *__restrict__ jobs, Stat
                 E rm[NC], lf[NC];
 #pragma unroll
                 for (int i = 0; i < NC; ++i) rm[i] = ((E)RH[i * N + n] + (E)RL[i * N + n]) * (E)S.invM[i];
-                job_lnf<NC, E>(S, J, rm, lf);
+                pr_lnf_v<NC, E>(JobView<E>{S, J}, rm, lf, nullptr);
                 const E c0 = PSI[n];
                 const E faces = (PSI[y * nx + xp] - c0) + (PSI[y * nx + xm] - c0) + (PSI[yp * nx + x] - c0) +
                                 (PSI[ym * nx + x] - c0);
@@ -192,9 +170,9 @@ __global__ void k_batch_round(const Shared S, const Job *__restrict__ jobs, Stat
                 for (int i = 0; i < NC; ++i) {
 #pragma unroll
                     for (int a = 0; a < 8; ++a) hv[i][a] = gin[(long long)(i * 8 + a) * N + n];
-                    const float *v = hv[i] - 1;
-                    jx += (v[1] - v[2]) + (v[5] - v[6]) + (v[7] - v[8]);
-                    jy += (v[3] - v[4]) + (v[5] - v[6]) + (v[8] - v[7]);
+                    const float *v = hv[i];  // v[a - 1] = g_a, a = 1..8
+                    jx += (v[0] - v[1]) + (v[4] - v[5]) + (v[6] - v[7]);
+                    jy += (v[2] - v[3]) + (v[4] - v[5]) + (v[7] - v[6]);
                 }
                 float Fx[NC], Fy[NC], ri[NC];
                 E Fsx = 0, Fsy = 0, rt = 0;
@@ -269,7 +247,7 @@ __global__ void k_batch_round(const Shared S, const Job *__restrict__ jobs, Stat
             __syncthreads();
         }
         // round end: change of the densities over the round, then store them
-        float dmax = 0.0f;
+        float dmax = 0.0f, rmax = 0.0f;
         bool finite = true;
         for (int k = t; k < NC * N; k += T) {
             const double now = (double)RH[k] + (double)RL[k];
@@ -277,19 +255,32 @@ __global__ void k_batch_round(const Shared S, const Job *__restrict__ jobs, Stat
             const float d = (float)fabs(now - was);
             finite = finite && isfinite(now);
             dmax = fmaxf(dmax, d);
+            rmax = fmaxf(rmax, RH[k]);
         }
         if (!finite) dmax = INFINITY;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_down_sync(0xffffffffu, dmax, o));
-        if ((t & 31) == 0) s_red[t >> 5] = dmax;
+        for (int o = 16; o > 0; o >>= 1) {
+            dmax = fmaxf(dmax, __shfl_down_sync(0xffffffffu, dmax, o));
+            rmax = fmaxf(rmax, __shfl_down_sync(0xffffffffu, rmax, o));
+        }
+        if ((t & 31) == 0) {
+            s_red[t >> 5] = dmax;
+            s_rmax[t >> 5] = rmax;
+        }
         __syncthreads();
         for (int k = t; k < NC * N; k += T) {
             pool[J.rh + k] = RH[k];
             pool[J.rl + k] = RL[k];
         }
         if (t == 0) {
-            float m = 0.0f;
-            for (int w = 0; w < (T + 31) / 32; ++w) m = fmaxf(m, s_red[w]);
+            float m = 0.0f, r = 0.0f;
+            for (int w = 0; w < (T + 31) / 32; ++w) {
+                m = fmaxf(m, s_red[w]);
+                r = fmaxf(r, s_rmax[w]);
+            }
+            // the stored populations are binary32: below 8 ulp of the largest
+            // density a change is their rounding jitter, not relaxation
+            const double bar = fmax(tol, 8.0 * ulp32(r));
             Status &st = status[jid];
             st.cur = cur;
             st.steps += steps;
@@ -297,7 +288,7 @@ __global__ void k_batch_round(const Shared S, const Job *__restrict__ jobs, Stat
             if (!(m <= 3.0e38f)) {           // non-finite densities: the job failed, retire it
                 st.converged = 2;
                 atomicAdd(n_converged, 1);
-            } else if (m < tol) {
+            } else if (m < bar) {
                 st.converged = 1;
                 atomicAdd(n_converged, 1);
             }

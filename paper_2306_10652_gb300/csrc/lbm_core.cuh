@@ -72,6 +72,17 @@ struct Params {
     float fRT, flnRT;
     float fb[kMaxNc], finvM[kMaxNc], fsqk[kMaxNc], frhobar[kMaxNc];
     float fA[kMaxNc * kMaxNc];
+    // double-binary32 (hi, lo) constants of the df64 thermodynamics
+    // (lbm_thermo_df.cuh), molar masses folded in
+    float2 dM[kMaxNc];           // 1 / M_i
+    float2 dB[kMaxNc];           // b_i / M_i
+    float2 db[kMaxNc];           // b_i
+    float2 dA[kMaxNc * kMaxNc];  // A_ij / M_j
+    float2 dRK[kMaxNc];          // RT (ln RT - ln M_i)
+    float2 dsqk[kMaxNc];         // sqrt(kappa_i)
+    float2 dPk[kMaxNc];          // sqrt(kappa_j) / M_j
+    float2 dRT;                  // RT
+    float4 logtab[128];          // df64 logarithm table (lbm_df64.cuh)
 };
 
 // Parameter access in the arithmetic type E of a kernel.
@@ -117,10 +128,20 @@ __device__ __forceinline__ float tdiv(float a, float b) { return __fdividef(a, b
 __device__ __forceinline__ double tlog(double x) { return log(x); }
 __device__ __forceinline__ float tlog(float x) { return __logf(x); }
 
-template <int NC, typename E = double>
-__device__ __forceinline__ void pr_lnf(const Params &P, const E (&rm)[NC], E (&lnf)[NC], E *p_out)
+// Constants of pr_lnf seen through a view: A(i, j) = (a alpha)_ij at the
+// problem's temperature, b(i), RT() and lnRT().  ParamsView reads a single
+// problem's block; the batched form supplies one per job (its own T).
+template <typename E> struct ParamsView {
+    const Params &P;
+    __device__ E A(int i, int j) const { return PV<E>::A(P, i * kMaxNc + j); }
+    __device__ E b(int i) const { return PV<E>::b(P, i); }
+    __device__ E RT() const { return PV<E>::RT(P); }
+    __device__ E lnRT() const { return PV<E>::lnRT(P); }
+};
+
+template <int NC, typename E, typename View>
+__device__ __forceinline__ void pr_lnf_v(const View &V, const E (&rm)[NC], E (&lnf)[NC], E *p_out)
 {
-    using V = PV<E>;
     const E kSqrt2 = (E)1.4142135623730951;
     E rho = 0;
 #pragma unroll
@@ -131,32 +152,38 @@ __device__ __forceinline__ void pr_lnf(const Params &P, const E (&rm)[NC], E (&l
     for (int i = 0; i < NC; ++i) x[i] = rm[i] * inv;
     E bm = 0;
 #pragma unroll
-    for (int i = 0; i < NC; ++i) bm = fma(x[i], V::b(P, i), bm);
+    for (int i = 0; i < NC; ++i) bm = fma(x[i], V.b(i), bm);
     E S[NC];
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
         E s = 0;
 #pragma unroll
-        for (int j = 0; j < NC; ++j) s = fma(V::A(P, i * kMaxNc + j), x[j], s);
+        for (int j = 0; j < NC; ++j) s = fma(V.A(i, j), x[j], s);
         S[i] = s;
     }
     E am = 0;
 #pragma unroll
     for (int i = 0; i < NC; ++i) am = fma(x[i], S[i], am);
-    const E RT = V::RT(P);
+    const E RT = V.RT();
     const E B = bm * rho;
     const E omB = (E)1 - B;
     const E den = fma(B, (E)2 - B, (E)1);  // 1 + 2B - B^2
     const E amr = tdiv(am * rho, RT);
     const E Zm1 = tdiv(B, omB) - tdiv(amr, den);
     const E Lr = tlog(tdiv(fma((E)1 + kSqrt2, B, (E)1), fma((E)1 - kSqrt2, B, (E)1)));
-    const E C0 = V::lnRT(P) - tlog(omB);
+    const E C0 = V.lnRT() - tlog(omB);
     const E invbm = tdiv((E)1, bm);
     const E C1 = Zm1 * invbm + tdiv(am * Lr * invbm * invbm, (E)2 * kSqrt2 * RT);
     const E C2 = tdiv(-Lr * invbm, kSqrt2 * RT);
 #pragma unroll
-    for (int i = 0; i < NC; ++i) lnf[i] = tlog(rm[i]) + C0 + fma(V::b(P, i), C1, S[i] * C2);
+    for (int i = 0; i < NC; ++i) lnf[i] = tlog(rm[i]) + C0 + fma(V.b(i), C1, S[i] * C2);
     if (p_out) *p_out = RT * rho / omB - am * rho * rho / den;
+}
+
+template <int NC, typename E = double>
+__device__ __forceinline__ void pr_lnf(const Params &P, const E (&rm)[NC], E (&lnf)[NC], E *p_out)
+{
+    pr_lnf_v<NC, E>(ParamsView<E>{P}, rm, lnf, p_out);
 }
 
 // Error-free binary32 transformations (Knuth TwoSum, Dekker fast TwoSum).

@@ -24,6 +24,7 @@
 #pragma once
 
 #include "lbm_internal.h"
+#include "lbm_thermo_df.cuh"
 
 namespace lbmfug {
 namespace fz {
@@ -329,16 +330,34 @@ __global__ void __launch_bounds__(kT)
     }
 }
 
+// Thermodynamics arithmetic of the binary32-state kernel: binary32 (LBM_FP32)
+// or double-binary32 (LBM_FP32DEV, lbm_thermo_df.cuh).  ET is the shared-
+// memory type of psi and mu: one binary32 value, or a (hi, lo) pair.
+struct DF64 {};
+template <typename E> struct ThermoT { using ET = float; };
+template <> struct ThermoT<DF64> { using ET = float2; };
+
 // Shared rows of the binary32 kernel have a fixed pitch of kT entries (a strip
 // needs at most W + 6 <= kT), so every row offset is a compile-time constant.
+// The exchange XC holds the collided values that move to the row above or
+// below in a neighbouring column (4 slots); values that stay in their row
+// move to the neighbouring column by warp shuffles, with the two lanes at a
+// warp's edges exchanging through BND.
 template <int NC, typename E> struct Smem32 {
+    using ET = typename ThermoT<E>::ET;
+    static constexpr bool kDF = sizeof(ET) == 8;
     static __host__ __device__ constexpr size_t rs(int) { return align16((size_t)4 * NC * kT * sizeof(float)); }
-    static __host__ __device__ constexpr size_t ps(int) { return align16((size_t)3 * kT * sizeof(E)); }
-    static __host__ __device__ constexpr size_t mu(int) { return align16((size_t)3 * NC * kT * sizeof(E)); }
-    static __host__ __device__ constexpr size_t xc() { return align16((size_t)6 * NC * kT * sizeof(float)); }
+    static __host__ __device__ constexpr size_t ps(int) { return align16((size_t)3 * kT * sizeof(ET)); }
+    static __host__ __device__ constexpr size_t mu(int) { return align16((size_t)3 * NC * kT * sizeof(ET)); }
+    static __host__ __device__ constexpr size_t xc() { return align16((size_t)4 * NC * kT * sizeof(float)); }
+    static __host__ __device__ constexpr size_t bnd() { return align16((size_t)(kT / 32) * 2 * NC * sizeof(float)); }
     static __host__ __device__ constexpr size_t red() { return align16((size_t)(kT / 32) * NC * sizeof(double)); }
     static __host__ __device__ constexpr size_t ms() { return align16((size_t)2 * NC * kT * sizeof(float)); }
-    static __host__ __device__ constexpr size_t total(int W) { return 2 * rs(W) + ps(W) + mu(W) + xc() + red() + ms(); }
+    static __host__ __device__ constexpr size_t lt() { return kDF ? (size_t)df::kLogTab * sizeof(float4) : 0; }
+    static __host__ __device__ constexpr size_t total(int W)
+    {
+        return lt() + 2 * rs(W) + ps(W) + mu(W) + xc() + bnd() + red() + ms();
+    }
 };
 constexpr int kWmax32 = kT - 6;  // binary32 kernel: one density column per thread
 
@@ -364,15 +383,19 @@ __global__ void __launch_bounds__(kT)
               double *__restrict__ mass_partials)
 {
     using L = Lattice<0>;
-    using V = PV<E>;
     using SM = Smem32<NC, E>;
+    using ET = typename SM::ET;
+    constexpr bool kDF = SM::kDF;
+    using VF = PV<float>;
     extern __shared__ __align__(16) unsigned char smem[];
-    float *RS = (float *)smem;                                   // [4][NC][kT] rho hi rows
-    float *RL = (float *)(smem + SM::rs(W));                     // [4][NC][kT] rho lo rows
-    E *PS = (E *)(smem + 2 * SM::rs(W));                         // [3][kT]     psi rows
-    E *MU = (E *)(smem + 2 * SM::rs(W) + SM::ps(W));             // [3][NC][kT] mu rows
-    float *XC = (float *)(smem + 2 * SM::rs(W) + SM::ps(W) + SM::mu(W));  // [6][NC][kT] exchange
-    double *RED = (double *)((unsigned char *)XC + SM::xc());
+    float4 *LT = (float4 *)smem;                                 // [128]      df64 log table
+    float *RS = (float *)(smem + SM::lt());                      // [4][NC][kT] rho hi rows
+    float *RL = (float *)(smem + SM::lt() + SM::rs(W));          // [4][NC][kT] rho lo rows
+    ET *PS = (ET *)(smem + SM::lt() + 2 * SM::rs(W));            // [3][kT]     psi rows
+    ET *MU = (ET *)((unsigned char *)PS + SM::ps(W));            // [3][NC][kT] mu rows
+    float *XC = (float *)((unsigned char *)MU + SM::mu(W));      // [4][NC][kT] exchange
+    float *BND = (float *)((unsigned char *)XC + SM::xc());      // [kT/32][2][NC] warp edges
+    double *RED = (double *)((unsigned char *)BND + SM::bnd());
     float *MS = (float *)((unsigned char *)RED + SM::red());     // [2][NC][kT] mass of rows written
     const float *gin = (const float *)in.g;
     float *gout = (float *)out.g;
@@ -387,18 +410,21 @@ __global__ void __launch_bounds__(kT)
     const int y0 = blockIdx.y * H;
     const int h = min(H, ny - y0);
     const int t = threadIdx.x;
+    const int lane = t & 31, warp = t >> 5;
     const int col = t - 1;
     const bool active = t < w + 2;
     const bool interior = col >= 0 && col < w;
+    const unsigned amask = __ballot_sync(0xffffffffu, active);
     const int xg = wrapc(x0 + col, nx);
     const int xd[3] = {wrapc(xg - 1, nx), xg, wrapc(xg + 1, nx)};
     // phase (A): one density column per thread (strips are at most kT - 6 wide)
     const int cA0 = t - 3;
     const bool hasA0 = cA0 < w + 3;
     const int xA0 = wrapc(x0 + cA0, nx);
-    const E RT = V::RT(P);
     const float om = (float)P.omega, om1 = (float)(1.0 - P.omega), cF = (float)(1.0 - 0.5 * P.omega);
 
+    if constexpr (kDF)
+        for (int j = t; j < df::kLogTab; j += kT) LT[j] = P.logtab[j];
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
         MS[(0 * NC + i) * kT + t] = 0.0f;
@@ -425,14 +451,20 @@ __global__ void __launch_bounds__(kT)
         {
             const int s4 = kk & 3, s3 = kk % 3;
             if (hasA0) {
-                E ps = 0;
 #pragma unroll
                 for (int i = 0; i < NC; ++i) {
                     RS[(s4 * NC + i) * CW + cA0 + 3] = rh0[i];
                     RL[(s4 * NC + i) * CW + cA0 + 3] = rl0[i];
-                    ps = fma(V::sqk(P, i), ((E)rh0[i] + (E)rl0[i]) * V::invM(P, i), ps);
                 }
-                PS[s3 * CW + cA0 + 3] = ps;
+                if constexpr (kDF) {
+                    const df::F2 ps = df::psi<NC>(P, rh0, rl0);
+                    PS[s3 * CW + cA0 + 3] = make_float2(ps.hi, ps.lo);
+                } else {
+                    float ps = 0.0f;
+#pragma unroll
+                    for (int i = 0; i < NC; ++i) ps = fmaf(VF::sqk(P, i), (rh0[i] + rl0[i]) * VF::invM(P, i), ps);
+                    PS[s3 * CW + cA0 + 3] = ps;
+                }
             }
         }
         __syncthreads();
@@ -440,24 +472,41 @@ __global__ void __launch_bounds__(kT)
         if (kk >= 2) {
             const int q = kk - 1;
             const int s4 = q & 3;
-            const E *p0 = PS + ((q + 2) % 3) * CW;
-            const E *p1 = PS + (q % 3) * CW;
-            const E *p2 = PS + ((q + 1) % 3) * CW;
+            const ET *p0 = PS + ((q + 2) % 3) * CW;
+            const ET *p1 = PS + (q % 3) * CW;
+            const ET *p2 = PS + ((q + 1) % 3) * CW;
             for (int c = t - 2; c < w + 2; c += kT) {
                 const int cc = c + 3;
-                E rm[NC], lf[NC];
+                if constexpr (kDF) {
+                    float hh[NC], ll[NC];
 #pragma unroll
-                for (int i = 0; i < NC; ++i) {
-                    rm[i] = ((E)RS[(s4 * NC + i) * CW + cc] + (E)RL[(s4 * NC + i) * CW + cc]) * V::invM(P, i);
+                    for (int i = 0; i < NC; ++i) {
+                        hh[i] = RS[(s4 * NC + i) * CW + cc];
+                        ll[i] = RL[(s4 * NC + i) * CW + cc];
+                    }
+                    const df::F2 lap = df::lap9(df::f2(p1[cc]), df::f2(p1[cc + 1]), df::f2(p1[cc - 1]),
+                                                df::f2(p2[cc]), df::f2(p0[cc]), df::f2(p2[cc + 1]),
+                                                df::f2(p2[cc - 1]), df::f2(p0[cc + 1]), df::f2(p0[cc - 1]));
+                    df::F2 mu[NC];
+                    df::mu<NC>(P, LT, hh, ll, lap, mu);
+#pragma unroll
+                    for (int i = 0; i < NC; ++i)
+                        MU[((q % 3) * NC + i) * CM + c + 2] = make_float2(mu[i].hi, mu[i].lo);
+                } else {
+                    float rm[NC], lf[NC];
+#pragma unroll
+                    for (int i = 0; i < NC; ++i)
+                        rm[i] = (RS[(s4 * NC + i) * CW + cc] + RL[(s4 * NC + i) * CW + cc]) * VF::invM(P, i);
+                    pr_lnf<NC, float>(P, rm, lf, nullptr);
+                    const float c0 = p1[cc];
+                    const float faces = (p1[cc + 1] - c0) + (p1[cc - 1] - c0) + (p2[cc] - c0) + (p0[cc] - c0);
+                    const float diags = (p2[cc + 1] - c0) + (p0[cc - 1] - c0) + (p0[cc + 1] - c0) + (p2[cc - 1] - c0);
+                    const float lap = 6.0f * fmaf(1.0f / 9.0f, faces, (1.0f / 36.0f) * diags);
+                    const float RT = VF::RT(P);
+#pragma unroll
+                    for (int i = 0; i < NC; ++i)
+                        MU[((q % 3) * NC + i) * CM + c + 2] = fmaf(RT, lf[i], -VF::sqk(P, i) * lap);
                 }
-                pr_lnf<NC, E>(P, rm, lf, nullptr);
-                const E c0 = p1[cc];
-                const E faces = (p1[cc + 1] - c0) + (p1[cc - 1] - c0) + (p2[cc] - c0) + (p0[cc] - c0);
-                const E diags = (p2[cc + 1] - c0) + (p0[cc - 1] - c0) + (p0[cc + 1] - c0) + (p2[cc - 1] - c0);
-                const E lap = (E)6 * fma((E)(1.0 / 9.0), faces, (E)(1.0 / 36.0) * diags);
-#pragma unroll
-                for (int i = 0; i < NC; ++i)
-                    MU[((q % 3) * NC + i) * CM + c + 2] = fma(RT, lf[i], -V::sqk(P, i) * lap);
             }
         }
         __syncthreads();
@@ -489,9 +538,9 @@ __global__ void __launch_bounds__(kT)
             const float *R0 = RS + ((q + 3) & 3) * NC * CW;
             const float *R1 = RS + (q & 3) * NC * CW;
             const float *R2 = RS + ((q + 1) & 3) * NC * CW;
-            const E *M0 = MU + ((q + 2) % 3) * NC * CM;
-            const E *M1 = MU + (q % 3) * NC * CM;
-            const E *M2 = MU + ((q + 1) % 3) * NC * CM;
+            const ET *M0 = MU + ((q + 2) % 3) * NC * CM;
+            const ET *M1 = MU + (q % 3) * NC * CM;
+            const ET *M2 = MU + ((q + 1) % 3) * NC * CM;
             const IDX rc = (IDX)yc * (IDX)nx + (IDX)xg;
             float hv[NC][8];
 #pragma unroll
@@ -501,34 +550,46 @@ __global__ void __launch_bounds__(kT)
             float jx = 0.0f, jy = 0.0f;
 #pragma unroll
             for (int i = 0; i < NC; ++i) {
-                const float *v = hv[i] - 1;  // v[a], a = 1..8
-                jx += (v[1] - v[2]) + (v[5] - v[6]) + (v[7] - v[8]);
-                jy += (v[3] - v[4]) + (v[5] - v[6]) + (v[8] - v[7]);
+                const float *v = hv[i];  // v[a - 1] = g_a, a = 1..8
+                jx += (v[0] - v[1]) + (v[4] - v[5]) + (v[6] - v[7]);
+                jy += (v[2] - v[3]) + (v[4] - v[5]) + (v[7] - v[6]);
             }
+            // Eq. (5): F_i = -rho~_i grad mu_i.  grad X = 3 sum_pairs w e (X(r+e) - X(r-e));
+            // with df64 mu every difference is taken on the (hi, lo) pairs and
+            // rounded once, so it carries the df64 accuracy of mu.
             float Fx[NC], Fy[NC], rlo1[NC];
-            E Fsx = 0, Fsy = 0, rt = 0;
+            float Fsx = 0.0f, Fsy = 0.0f, rt = 0.0f;
 #pragma unroll
             for (int i = 0; i < NC; ++i) {
-                const E *m0 = M0 + i * CM, *m1 = M1 + i * CM, *m2 = M2 + i * CM;
-                const E dE = m1[cm + 1] - m1[cm - 1];
-                const E dN = m2[cm] - m0[cm];
-                const E dNE = m2[cm + 1] - m0[cm - 1];
-                const E dSE = m0[cm + 1] - m2[cm - 1];
-                const E gx = (E)3 * fma((E)(1.0 / 9.0), dE, (E)(1.0 / 36.0) * (dNE + dSE));
-                const E gy = (E)3 * fma((E)(1.0 / 9.0), dN, (E)(1.0 / 36.0) * (dNE - dSE));
+                const ET *m0 = M0 + i * CM, *m1 = M1 + i * CM, *m2 = M2 + i * CM;
+                float dE, dN, dNE, dSE;
+                if constexpr (kDF) {
+                    const float2 e1 = m1[cm + 1], w1 = m1[cm - 1], n1 = m2[cm], s1 = m0[cm];
+                    const float2 ne = m2[cm + 1], sw = m0[cm - 1], se = m0[cm + 1], nw = m2[cm - 1];
+                    dE = (e1.x - w1.x) + (e1.y - w1.y);
+                    dN = (n1.x - s1.x) + (n1.y - s1.y);
+                    dNE = (ne.x - sw.x) + (ne.y - sw.y);
+                    dSE = (se.x - nw.x) + (se.y - nw.y);
+                } else {
+                    dE = m1[cm + 1] - m1[cm - 1];
+                    dN = m2[cm] - m0[cm];
+                    dNE = m2[cm + 1] - m0[cm - 1];
+                    dSE = m0[cm + 1] - m2[cm - 1];
+                }
+                const float gx = 3.0f * fmaf(1.0f / 9.0f, dE, (1.0f / 36.0f) * (dNE + dSE));
+                const float gy = 3.0f * fmaf(1.0f / 9.0f, dN, (1.0f / 36.0f) * (dNE - dSE));
                 rlo1[i] = RL[((q & 3) * NC + i) * CW + cc];
-                const E ri = (E)R1[i * CW + cc] + (E)rlo1[i];
+                const float ri = R1[i * CW + cc] + rlo1[i];
                 rt += ri;
-                const E rmi = ri * V::invM(P, i);
-                const E fx = -rmi * gx, fy = -rmi * gy;
-                Fsx += fx;
-                Fsy += fy;
-                Fx[i] = (float)fx;
-                Fy[i] = (float)fy;
+                const float rmi = ri * VF::invM(P, i);
+                Fx[i] = -rmi * gx;
+                Fy[i] = -rmi * gy;
+                Fsx += Fx[i];
+                Fsy += Fy[i];
             }
-            const E irt = tdiv((E)1, rt);
-            const float ux = (float)(fma((E)0.5, Fsx, (E)jx) * irt);
-            const float uy = (float)(fma((E)0.5, Fsy, (E)jy) * irt);
+            const float irt = __fdividef(1.0f, rt);
+            const float ux = fmaf(0.5f, Fsx, jx) * irt;
+            const float uy = fmaf(0.5f, Fsy, jy) * irt;
             const float u2 = ux * ux + uy * uy;
             // Eqs. (1a)-(1c) over the four pairs of opposite directions (a, a+1):
             //   g*_a = (1 - w) g_a + sym +- anti,
@@ -559,7 +620,7 @@ __global__ void __launch_bounds__(kT)
                 const float Gu = Gx * ux + Gy * uy;
                 // class term: faces -Gu/2 - 3F.u, diagonals Gu - 3F.u
                 const float Kf = fmaf(-0.5f, Gu, -Fu3), Kd = Gu - Fu3;
-                const float *v = hv[i] - 1;  // v[a], a = 1..8
+                const float *v = hv[i];  // v[a - 1] = g_a, a = 1..8
 #pragma unroll
                 for (int p = 0; p < 4; ++p) {
                     const int a = 2 * p + 1;  // e_{a+1} = -e_a
@@ -570,8 +631,8 @@ __global__ void __launch_bounds__(kT)
                     const float S = fmaf(U3[p], fmaf(3.0f, Fe, Ge), (ex != 0 && ey != 0) ? Kd : Kf);
                     const float sym = fmaf(ri, WBs[p], cw * S);
                     const float anti = fmaf(ri, WBa[p], (3.0f * cw) * Fe);
-                    const float gp = fmaf(om1, v[a], sym + anti);
-                    const float gm = fmaf(om1, v[a + 1], sym - anti);
+                    const float gp = fmaf(om1, v[a - 1], sym + anti);
+                    const float gm = fmaf(om1, v[a], sym - anti);
                     // each departure leaves the pair of row crow (bH, bL) by its own Fast2Sum
                     pair_acc(bH[i], bL[i], -gp);
                     pair_acc(bH[i], bL[i], -gm);
@@ -584,9 +645,20 @@ __global__ void __launch_bounds__(kT)
                         if (bx == 0) {
                             if (by < 0) own0[i] = gs;
                             else own2[i] = gs;
-                        } else {
-                            XC[(((by + 1) * 2 + (bx > 0 ? 0 : 1)) * NC + i) * kT + t] = gs;
+                        } else if (by != 0) {
+                            XC[((((by + 1) >> 1) * 2 + (bx > 0 ? 0 : 1)) * NC + i) * kT + t] = gs;
                         }
+                    }
+                    if (ey == 0) {
+                        // same-row arrivals: the left neighbour's +x value and the
+                        // right neighbour's -x value, by shuffle within the warp;
+                        // the warp's edge lanes take theirs from BND after the barrier
+                        const float fromL = __shfl_up_sync(amask, gp, 1);
+                        const float fromR = __shfl_down_sync(amask, gm, 1);
+                        if (lane == 31) BND[(warp * 2 + 0) * NC + i] = gp;
+                        if (lane == 0) BND[(warp * 2 + 1) * NC + i] = gm;
+                        if (lane > 0) pair_acc(bH[i], bL[i], fromL);
+                        if (lane < 31) pair_acc(bH[i], bL[i], fromR);
                     }
                 }
             }
@@ -622,17 +694,18 @@ __global__ void __launch_bounds__(kT)
                     MS[(0 * NC + i) * kT + t] = ms;
                     MS[(1 * NC + i) * kT + t] = mc + lo;
                 }
-                // row crow (its departures left during the collision): arrivals along the row
+                // row crow (its departures and in-warp same-row arrivals were
+                // applied during the collision): the edge lanes' arrivals
                 aH[i] = bH[i];
                 aL[i] = bL[i];
-                pair_acc(aH[i], aL[i], xc[2 * NC * kT + t - 1]);
-                pair_acc(aH[i], aL[i], xc[3 * NC * kT + t + 1]);
+                if (lane == 0) pair_acc(aH[i], aL[i], BND[((warp - 1) * 2 + 0) * NC + i]);
+                if (lane == 31) pair_acc(aH[i], aL[i], BND[((warp + 1) * 2 + 1) * NC + i]);
                 // row crow+1: its old density, then the first arrivals
                 bH[i] = Rh2[i * CW + cc];
                 bL[i] = RL[(((q + 1) & 3) * NC + i) * CW + cc];
-                pair_acc(bH[i], bL[i], xc[4 * NC * kT + t - 1]);
+                pair_acc(bH[i], bL[i], xc[2 * NC * kT + t - 1]);
                 pair_acc(bH[i], bL[i], own2[i]);
-                pair_acc(bH[i], bL[i], xc[5 * NC * kT + t + 1]);
+                pair_acc(bH[i], bL[i], xc[3 * NC * kT + t + 1]);
             }
         }
     }

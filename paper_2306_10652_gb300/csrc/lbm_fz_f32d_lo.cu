@@ -1,3 +1,3 @@
-// Fused D2Q9 instantiations: storage float, thermodynamics double, Nc 1..8.
+// Fused D2Q9 instantiations: storage float, thermodynamics double-binary32, Nc 1..8.
 #include "lbm_fused2d.cuh"
-LBM_FZ_TU(f32d_lo, float, double, 1, 8)
+LBM_FZ_TU(f32d_lo, float, DF64, 1, 8)

@@ -73,6 +73,15 @@ int launch_fused_step(int prec, int nc, const Params &P, const FusedGeom &geo, S
 int launch_fused_mass_final(int nc, const FusedGeom &geo, const double *partials, double *out,
                             int *nonfinite, cudaStream_t s);
 
+// Chemical potentials and forces of a D2Q9 state from its binary64 densities
+// (lbm_fields_*.cu).  prec: 0 binary64, 1 double-binary32, 2 binary32
+// thermodynamics.  scratch: (nc + 1) * N * 8 bytes; F [nc][2][N], mu [nc][N]
+// (mu may be null).
+int launch_forces_lo(int prec, int nc, const Params &P, const double *rho, void *scratch, double *F,
+                     double *mu, cudaStream_t s);
+int launch_forces_hi(int prec, int nc, const Params &P, const double *rho, void *scratch, double *F,
+                     double *mu, cudaStream_t s);
+
 // Deterministic reductions (lbm_reduce.cu).  Partials: [blocks][nc].
 constexpr int kReduceBlocks = 1216;  // 8 x 152 SMs
 constexpr int kReduceThreads = 256;

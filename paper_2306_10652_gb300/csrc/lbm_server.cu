@@ -13,12 +13,14 @@
 // latency, which frees their memory for the queue.  Because every job is an
 // independent handle with deterministic kernels, a job's result is the same
 // alone and in the mix.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
 #include <map>
 #include <memory>
+#include <cmath>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -35,6 +37,7 @@ struct Request {
     int lattice = 0, nx = 0, ny = 0, nz = 0, nc = 0, precision = LBM_FP32DEV, check_every = 1000;
     std::vector<double> a, b, omega, kij, M, rho;
     double T = 0, tau = 1, kappa_ref = 0.02, tol = 1e-10;
+    double bar = 1e-10;  // the convergence bar in use: tol, or 8 binary32 ulp of the largest density
     long long max_steps = 0;
     size_t bytes = 0;
     int state = 0;  // 0 queued, 1 running, 2 converged, 3 failed, 4 exhausted (max_steps)
@@ -118,6 +121,16 @@ struct lbm_server {
             finish(r, 3);
             return false;
         }
+        // binary32 storage jitters at the rounding of its populations: changes
+        // below 8 ulp of binary32 at the largest density count as converged
+        r->bar = r->tol;
+        if (r->precision != LBM_FP64) {
+            double rmax = 0.0;
+            for (double v : r->rho) rmax = std::max(rmax, v);
+            int e = 0;
+            std::frexp(1.05 * rmax, &e);  // 1.05 rmax in [2^(e-1), 2^e)
+            r->bar = std::max(r->tol, 8.0 * std::ldexp(1.0, e - 1 - 23));
+        }
         r->rho.clear();
         r->rho.shrink_to_fit();
         return true;
@@ -164,7 +177,7 @@ struct lbm_server {
                 if (st) {
                     r->error = st;
                     finish(r, 3);
-                } else if (d < r->tol) {
+                } else if (d < r->bar) {
                     finish(r, 2);
                 } else if (r->steps >= r->max_steps) {
                     finish(r, 4);

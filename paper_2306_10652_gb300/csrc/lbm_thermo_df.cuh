@@ -1,0 +1,144 @@
+// lbm_thermo_df.cuh -- the Peng-Robinson chemical potentials of one node in
+// double-binary32 arithmetic (lbm_df64.cuh), for the binary32-storage kernels
+// whose thermodynamics keep binary64 accuracy (LBM_FP32DEV).
+//
+// Paper: Soomro & Ayala, arXiv 2306.10652.
+//   Sec. 2.1, Eq. (4)-(5)  interface term sum_j kappa_ij lap rho~_j with
+//                          kappa_ij = sqrt(kappa_i kappa_j) = sqrt(kappa_i) lap psi,
+//                          psi = sum_j sqrt(kappa_j) rho~_j
+//   Sec. 2.2, Eq. (6)      kappa_i = kappa_ref a_i / a_ref
+//   Sec. 2.3, Eqs. (9)-(12) PR mixture and fugacities
+//
+// Evaluated from the mass densities rho_j = h_j + l_j (the exact binary32
+// pair of the state) with the molar masses folded into the constants
+// (rho~_j = rho_j / M_j).  With B = b_m rho~ = sum_j (b_j / M_j) rho_j,
+// T_i = rho~ S_i = sum_j (A_ij / M_j) rho_j and Q = rho~^2 (a alpha)_m =
+// sum_i rho~_i T_i, the regrouped Eq. (12) (the printed form plus ln(x_i p),
+// so that p cancels and it holds for p <= 0 too) reads
+//   RT ln f_i = RT ln rho_i + RT (ln RT - ln M_i) - RT ln(1 - B)
+//               + b_i RT C1 + T_i RT C2',
+//   RT C1  = RT rho~ / (1 - B) + (Q / B) [Lr / (2 sqrt2 B) - 1 / (1 + 2B - B^2)],
+//   RT C2' = -Lr / (sqrt2 B),  Lr = ln[(1 + (1 + sqrt2) B) / (1 + (1 - sqrt2) B)],
+// and mu_i = RT ln f_i - sqrt(kappa_i) lap psi (Eq. 5 rewritten through
+// Eq. 4).  Every step is a df64 operation; the result's absolute error is
+// about 2^-44 of the largest term.
+#pragma once
+
+#include "lbm_core.cuh"
+#include "lbm_df64.cuh"
+
+namespace lbmfug {
+namespace df {
+
+__device__ __forceinline__ F2 f2(float2 v) { return {v.x, v.y}; }
+
+// unnormalised product (for accumulation into a compensated sum)
+__device__ __forceinline__ F2 mul_u(F2 a, F2 b)
+{
+    const F2 p = two_prod(a.hi, b.hi);
+    return {p.hi, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo))};
+}
+
+// psi = sum_j sqrt(kappa_j) rho~_j at one node (Eq. 4)
+template <int NC>
+__device__ __forceinline__ F2 psi(const Params &P, const float (&h)[NC], const float (&l)[NC])
+{
+    Dot d;
+    d.first(f2(P.dPk[0]), {h[0], l[0]});
+#pragma unroll
+    for (int j = 1; j < NC; ++j) d.add(f2(P.dPk[j]), {h[j], l[j]});
+    return d.value();
+}
+
+// D2Q9 lap X = (2/cs2) sum_a w_a (X(r + e_a) - X(r))
+//            = (4 (faces) + (diagonals) - 20 X(r)) / 6
+__device__ __forceinline__ F2 lap9(F2 c, F2 e, F2 w, F2 n, F2 s, F2 ne, F2 nw, F2 se, F2 sw)
+{
+    Dot a;
+    a.s = __fmul_rn(4.0f, e.hi);
+    a.c = __fmul_rn(4.0f, e.lo);
+    a.add_term({__fmul_rn(4.0f, w.hi), __fmul_rn(4.0f, w.lo)});
+    a.add_term({__fmul_rn(4.0f, n.hi), __fmul_rn(4.0f, n.lo)});
+    a.add_term({__fmul_rn(4.0f, s.hi), __fmul_rn(4.0f, s.lo)});
+    a.add_term(ne);
+    a.add_term(nw);
+    a.add_term(se);
+    a.add_term(sw);
+    const F2 c20 = two_prod(-20.0f, c.hi);
+    a.add_term({c20.hi, fmaf(-20.0f, c.lo, c20.lo)});
+    return mul(a.value(), {hi_of(1.0 / 6.0), lo_of(1.0 / 6.0)});
+}
+
+// mu_i = RT ln f_i - sqrt(kappa_i) lap psi for i < NC at one node
+template <int NC>
+__device__ __forceinline__ void mu(const Params &P, const float4 *__restrict__ tab, const float (&h)[NC],
+                                   const float (&l)[NC], F2 lap, F2 (&out)[NC])
+{
+    constexpr double kS2 = 1.41421356237309504880168872421;
+    // rho~_i and rho~ = sum_i rho~_i
+    F2 y[NC];
+    Dot rt;
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+        y[i] = Dot::term(f2(P.dM[i]), {h[i], l[i]});
+        if (i == 0) {
+            rt.s = y[0].hi;
+            rt.c = y[0].lo;
+        } else {
+            rt.add_term(y[i]);
+        }
+    }
+    const F2 rho = rt.value();
+    // Eq. (11) times rho~: B = b_m rho~
+    Dot bd;
+    bd.first(f2(P.dB[0]), {h[0], l[0]});
+#pragma unroll
+    for (int j = 1; j < NC; ++j) bd.add(f2(P.dB[j]), {h[j], l[j]});
+    const F2 B = bd.value();
+    // Eq. (10): T_i = rho~ sum_j x_j (a alpha)_ij, Q = rho~^2 (a alpha)_m
+    F2 T[NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+        Dot t;
+        t.first(f2(P.dA[i * kMaxNc]), {h[0], l[0]});
+#pragma unroll
+        for (int j = 1; j < NC; ++j) t.add(f2(P.dA[i * kMaxNc + j]), {h[j], l[j]});
+        T[i] = t.value();
+    }
+    Dot qd;
+    qd.first(y[0], T[0]);
+#pragma unroll
+    for (int i = 1; i < NC; ++i) qd.add(y[i], T[i]);
+    const F2 Q = qd.value();
+    // per-node terms of Eq. (12)
+    const F2 one = {1.0f, 0.0f};
+    const F2 omB = add(one, neg(B));
+    const F2 den = add(one, mul(B, add({2.0f, 0.0f}, neg(B))));  // 1 + 2B - B^2
+    const F2 N1 = add(one, mul(B, {hi_of(1.0 + kS2), lo_of(1.0 + kS2)}));
+    const F2 N2 = add(one, mul(B, {hi_of(1.0 - kS2), lo_of(1.0 - kS2)}));
+    const F2 Lr = norm(log(div(N1, N2), tab));
+    const F2 lnomB = norm(log(omB, tab));
+    const F2 u = div(one, B), v = div(one, omB), w = div(one, den);
+    const F2 RT = f2(P.dRT);
+    const F2 Lu = mul(Lr, u);
+    const F2 RC1 = add(mul(mul(RT, rho), v),
+                       mul(mul(Q, u), add(mul(Lu, {hi_of(0.5 / kS2), lo_of(0.5 / kS2)}), neg(w))));
+    const F2 RC2 = mul(Lu, {hi_of(-1.0 / kS2), lo_of(-1.0 / kS2)});
+    const F2 RG = mul(RT, lnomB);
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+        Dot a;  // compensated sum of the terms of mu_i
+        const F2 t0 = mul_u(RT, log({h[i], l[i]}, tab));
+        a.s = t0.hi;
+        a.c = t0.lo;
+        a.add_term(f2(P.dRK[i]));
+        a.add_term(neg(RG));
+        a.add_term(mul_u(f2(P.db[i]), RC1));
+        a.add_term(mul_u(T[i], RC2));
+        a.add_term(neg(mul_u(f2(P.dsqk[i]), lap)));
+        out[i] = a.value();
+    }
+}
+
+}  // namespace df
+}  // namespace lbmfug

@@ -60,6 +60,8 @@ _sig("lbm_step", ctypes.c_int, _vp, ctypes.c_longlong)
 _sig("lbm_moments", ctypes.c_int, _vp, _dp, _dp, _dp, _dp)
 _sig("lbm_moments_device", ctypes.c_int, _vp, _vp, _vp, _vp, _vp)
 _sig("lbm_mass", ctypes.c_int, _vp, _dp)
+_sig("lbm_forces", ctypes.c_int, _vp, _dp, _dp)
+_sig("lbm_schedule_info", ctypes.c_int, _vp, _ip, _ip, _ip, _ip, _ip)
 _sig("lbm_convergence", ctypes.c_int, _vp, _dp)
 _sig("lbm_get_state", ctypes.c_int, _vp, _dp, ctypes.POINTER(ctypes.c_size_t))
 _sig("lbm_set_state", ctypes.c_int, _vp, _dp, ctypes.c_size_t)
@@ -247,6 +249,19 @@ class Problem:
         m = np.empty(self.nc)
         _check(_lib.lbm_mass(self._h, _hp(m)), "lbm_mass")
         return m
+
+    def forces(self, want=("F", "mu")):
+        """{"F": [Nc, 2, nz, ny, nx], "mu": [Nc, nz, ny, nx]} (lbm_forces, D2Q9)."""
+        F = np.empty((self.nc, 2) + self.shape) if "F" in want else None
+        mu = np.empty((self.nc,) + self.shape) if "mu" in want else None
+        _check(_lib.lbm_forces(self._h, _hp(F), _hp(mu)), "lbm_forces")
+        return {k: v for k, v in (("F", F), ("mu", mu)) if v is not None}
+
+    def schedule_info(self):
+        """dict(fused, strip, nstrips, seg_h, segs) of the step's launch geometry."""
+        v = [ctypes.c_int() for _ in range(5)]
+        _check(_lib.lbm_schedule_info(self._h, *[ctypes.byref(x) for x in v]), "lbm_schedule_info")
+        return dict(zip(("fused", "strip", "nstrips", "seg_h", "segs"), (x.value for x in v)))
 
     def convergence(self):
         v = ctypes.c_double()

@@ -496,3 +496,24 @@ def test_multiphase_rachford_rice_reduces_to_two_phases():
     assert r is not None
     assert abs(r.beta[0] - f2.beta) < 1e-9
     assert np.abs(r.x[0] - f2.y).max() < 1e-9 and np.abs(r.x[1] - f2.x).max() < 1e-9
+
+
+def test_oracle_threads_do_not_change_results():
+    """The oracle's OpenMP node loops compute every value on one thread in
+    the serial order: one thread and every core give bitwise equal steps."""
+    from oracle.orc import set_threads
+    P = synthetic_problem(17, 3, shape=(1, 64, 80), Tfac=0.9)
+    rho = synth.random_state(17, 3, (1, 64, 80), 0.05, 0.5) / P.b[:, None, None, None] / 3
+    g0 = P.init_equilibrium(rho)
+    try:
+        set_threads(1)
+        g1 = P.step(g0, 2)
+        m1 = P.moments(g1)
+        n = set_threads(0)
+        g2 = P.step(g0, 2)
+        m2 = P.moments(g2)
+    finally:
+        set_threads(0)
+    assert np.array_equal(g1, g2) and n >= 1
+    for k in m1:
+        assert np.array_equal(m1[k], m2[k]), k
