@@ -38,6 +38,7 @@ struct lbm_problem {
     double *snap = nullptr;
     bool have_snap = false;
     void *fscratch = nullptr;  // psi / mu scratch of lbm_forces
+    float2 *mu = nullptr;      // [nc][N] chemical potentials of the LBM_FP32DEV step
     long long launches = 0;
     long long monitor_step = -1;
     double *mon = nullptr;  // [nc] latest monitored mass
@@ -222,6 +223,10 @@ int ensure_allocated(lbm_problem *p)
         p->mass_partials =
             (double *)dev_alloc(p, (size_t)p->geo.nstrips * p->geo.segs * p->nc * sizeof(double));
         if (!p->mass_partials || p->geo.nstrips < 1) return LBM_ENOMEM;
+        if (p->opt.precision == LBM_FP32DEV) {
+            p->mu = (float2 *)dev_alloc(p, nf * sizeof(float2));
+            if (!p->mu || p->geo.mnstrips < 1) return LBM_ENOMEM;
+        }
     }
     if (cudaMemsetAsync(p->flag, 0, 16, p->stream) != cudaSuccess) return LBM_ECUDA;
     p->allocated = true;
@@ -385,9 +390,11 @@ int lbm_step(lbm_problem *p, long long n)
         const bool mon = every > 0 && ((p->steps + 1) % every == 0);
         int e;
         if (p->fused) {
+            int nl = 0;
             e = launch_fused_step(p->opt.precision, p->nc, p->P, p->geo, p->st[p->cur],
-                                  p->st[p->cur ^ 1], mon ? p->mass_partials : nullptr, p->stream);
-            p->launches += 1;
+                                  p->st[p->cur ^ 1], mon ? p->mass_partials : nullptr, p->mu, &nl,
+                                  p->stream);
+            p->launches += nl;
             if (!e && mon) {
                 e = launch_fused_mass_final(p->nc, p->geo, p->mass_partials, p->mon, p->flag, p->stream);
                 p->launches += 1;

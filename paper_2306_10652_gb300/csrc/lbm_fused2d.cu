@@ -84,6 +84,17 @@ FusedGeom fused_geometry(int prec, int nc, const Params &P, int num_sms)
     if (segs > P.ny) segs = P.ny;
     g.seg_h = (int)((P.ny + segs - 1) / segs);
     g.segs = (P.ny + g.seg_h - 1) / g.seg_h;
+    const int mper_sm = o->occupancy_mu();
+    if (mper_sm > 0) {
+        // mu pass: strips of at most kT - 2 columns, segments filling every slot
+        g.mnstrips = (P.nx + fz::kWmaxMu - 1) / fz::kWmaxMu;
+        g.mstrip = (P.nx + g.mnstrips - 1) / g.mnstrips;
+        long long ms = (long long)num_sms * mper_sm / g.mnstrips;
+        if (ms < 1) ms = 1;
+        if (ms > P.ny) ms = P.ny;
+        g.mseg_h = (int)((P.ny + ms - 1) / ms);
+        g.msegs = (P.ny + g.mseg_h - 1) / g.mseg_h;
+    }
     return g;
 }
 
@@ -94,10 +105,10 @@ int launch_fused_density(int prec, int nc, const Params &P, StateBufs st, cudaSt
 }
 
 int launch_fused_step(int prec, int nc, const Params &P, const FusedGeom &geo, StateBufs in,
-                      StateBufs out, double *mass_partials, cudaStream_t s)
+                      StateBufs out, double *mass_partials, float2 *mu, int *launches, cudaStream_t s)
 {
     const fz::Ops *o = lookup(prec, nc);
-    return o ? o->step(P, geo, in, out, mass_partials, s) : (int)cudaErrorInvalidValue;
+    return o ? o->step(P, geo, in, out, mass_partials, mu, launches, s) : (int)cudaErrorInvalidValue;
 }
 
 int launch_fused_mass_final(int nc, const FusedGeom &geo, const double *partials, double *out,

@@ -23,6 +23,8 @@
 // force arithmetic E (double or float), collision arithmetic S.
 #pragma once
 
+#include <type_traits>
+
 #include "lbm_internal.h"
 #include "lbm_thermo_df.cuh"
 
@@ -330,36 +332,101 @@ __global__ void __launch_bounds__(kT)
     }
 }
 
-// Thermodynamics arithmetic of the binary32-state kernel: binary32 (LBM_FP32)
-// or double-binary32 (LBM_FP32DEV, lbm_thermo_df.cuh).  ET is the shared-
-// memory type of psi and mu: one binary32 value, or a (hi, lo) pair.
+// Thermodynamics arithmetic of the binary32-state kernel: binary32 (LBM_FP32,
+// evaluated inside the step kernel) or double-binary32 (LBM_FP32DEV: a
+// separate pass, k_mu32, writes mu as (hi, lo) pairs, which the step kernel
+// reads).  ET is the shared-memory type of mu: one binary32 value, or a pair.
 struct DF64 {};
 template <typename E> struct ThermoT { using ET = float; };
 template <> struct ThermoT<DF64> { using ET = float2; };
 
 // Shared rows of the binary32 kernel have a fixed pitch of kT entries (a strip
 // needs at most W + 6 <= kT), so every row offset is a compile-time constant.
-// The exchange XC holds the collided values that move to the row above or
-// below in a neighbouring column (4 slots); values that stay in their row
-// move to the neighbouring column by warp shuffles, with the two lanes at a
-// warp's edges exchanging through BND.
+// The exchange XC holds the collided values that move to a neighbouring
+// column (6 slots: row below, same row, row above; to the right or left).
 template <int NC, typename E> struct Smem32 {
     using ET = typename ThermoT<E>::ET;
     static constexpr bool kDF = sizeof(ET) == 8;
     static __host__ __device__ constexpr size_t rs(int) { return align16((size_t)4 * NC * kT * sizeof(float)); }
-    static __host__ __device__ constexpr size_t ps(int) { return align16((size_t)3 * kT * sizeof(ET)); }
+    static __host__ __device__ constexpr size_t ps(int) { return kDF ? 0 : align16((size_t)3 * kT * sizeof(float)); }
     static __host__ __device__ constexpr size_t mu(int) { return align16((size_t)3 * NC * kT * sizeof(ET)); }
-    static __host__ __device__ constexpr size_t xc() { return align16((size_t)4 * NC * kT * sizeof(float)); }
-    static __host__ __device__ constexpr size_t bnd() { return align16((size_t)(kT / 32) * 2 * NC * sizeof(float)); }
+    static __host__ __device__ constexpr size_t xc() { return align16((size_t)6 * NC * kT * sizeof(float)); }
     static __host__ __device__ constexpr size_t red() { return align16((size_t)(kT / 32) * NC * sizeof(double)); }
     static __host__ __device__ constexpr size_t ms() { return align16((size_t)2 * NC * kT * sizeof(float)); }
-    static __host__ __device__ constexpr size_t lt() { return kDF ? (size_t)df::kLogTab * sizeof(float4) : 0; }
     static __host__ __device__ constexpr size_t total(int W)
     {
-        return lt() + 2 * rs(W) + ps(W) + mu(W) + xc() + bnd() + red() + ms();
+        return 2 * rs(W) + ps(W) + mu(W) + xc() + red() + ms();
     }
 };
 constexpr int kWmax32 = kT - 6;  // binary32 kernel: one density column per thread
+constexpr int kWmaxMu = kT - 2;  // mu pass: psi on one halo column each side
+
+// Double-binary32 chemical potentials (LBM_FP32DEV), one pass before the step
+// kernel.  Each CTA walks a segment of rows of a strip of W <= kT - 2
+// columns: for row k it forms psi(k) (Eq. 4) on columns [-1, W] from the
+// state's exact density pairs, then mu of row k-1 (Eqs. 5, 9-12 through
+// lbm_thermo_df.cuh) on the interior columns from psi rows k-2..k and the
+// pairs of row k-1 it kept from the previous row, and writes it to
+// mu[i][node] as (hi, lo).  psi rows live in a ring of four, so one barrier
+// per row suffices (a row's slot is rewritten only after every thread has
+// passed the barrier that follows its last reader).
+template <int NC, typename IDX>
+__global__ void __launch_bounds__(kT) k_mu32(const Params P, const int W, const int H, StateBufs in,
+                                             float2 *__restrict__ mug)
+{
+    __shared__ float4 LT[df::kLogTab];
+    __shared__ float2 PS[4][kT];
+    const int nx = P.nx, ny = P.ny;
+    const IDX N = (IDX)P.N;
+    const int x0 = blockIdx.x * W;
+    const int w = min(W, nx - x0);
+    const int y0 = blockIdx.y * H;
+    const int h = min(H, ny - y0);
+    const int t = threadIdx.x;
+    const int c = t - 1;  // column of this thread, -1 .. w
+    const bool has = c <= w;
+    const bool interior = c >= 0 && c < w;
+    const int xg = wrapc(x0 + c, nx);
+    const float *rhin = in.rhi_f();
+    const float *rlin = in.rlo;
+    for (int j = t; j < df::kLogTab; j += kT) LT[j] = P.logtab[j];
+    float ph[NC], pl[NC];  // density pairs of row k-1 at this column
+#pragma unroll
+    for (int i = 0; i < NC; ++i) ph[i] = pl[i] = 0.0f;
+    for (int kk = 0; kk < h + 2; ++kk) {
+        const int k = y0 - 1 + kk;
+        float hh[NC], ll[NC];
+        if (has) {
+            const IDX rb = (IDX)wrapc(k, ny) * (IDX)nx + (IDX)xg;
+#pragma unroll
+            for (int i = 0; i < NC; ++i) {
+                hh[i] = __ldg(rhin + i * N + rb);
+                ll[i] = __ldg(rlin + i * N + rb);
+            }
+            const df::F2 ps = df::psi<NC>(P, hh, ll);
+            PS[kk & 3][t] = make_float2(ps.hi, ps.lo);
+        }
+        __syncthreads();
+        if (kk >= 2 && interior) {
+            const float2 *p0 = PS[(kk - 2) & 3], *p1 = PS[(kk - 1) & 3], *p2 = PS[kk & 3];
+            const df::F2 lap = df::lap9(df::f2(p1[t]), df::f2(p1[t + 1]), df::f2(p1[t - 1]), df::f2(p2[t]),
+                                        df::f2(p0[t]), df::f2(p2[t + 1]), df::f2(p2[t - 1]), df::f2(p0[t + 1]),
+                                        df::f2(p0[t - 1]));
+            df::F2 m[NC];
+            df::mu<NC>(P, LT, ph, pl, lap, m);
+            const IDX ob = (IDX)wrapc(k - 1, ny) * (IDX)nx + (IDX)xg;
+#pragma unroll
+            for (int i = 0; i < NC; ++i) mug[i * N + ob] = make_float2(m[i].hi, m[i].lo);
+        }
+        if (has) {
+#pragma unroll
+            for (int i = 0; i < NC; ++i) {
+                ph[i] = hh[i];
+                pl[i] = ll[i];
+            }
+        }
+    }
+}
 
 // Binary32 state: the 8 moving populations g[i][a-1][node] (a = 1..8) and the
 // density rho_i = hi + lo.  Collision arithmetic in binary32; thermodynamics
@@ -380,7 +447,7 @@ __device__ __forceinline__ void pair_acc(float &hi, float &lo, float x)
 template <int NC, typename E, typename IDX>
 __global__ void __launch_bounds__(kT)
     k_fused32(const Params P, const int W, const int H, StateBufs in, StateBufs out,
-              double *__restrict__ mass_partials)
+              double *__restrict__ mass_partials, const float2 *__restrict__ mug)
 {
     using L = Lattice<0>;
     using SM = Smem32<NC, E>;
@@ -388,14 +455,12 @@ __global__ void __launch_bounds__(kT)
     constexpr bool kDF = SM::kDF;
     using VF = PV<float>;
     extern __shared__ __align__(16) unsigned char smem[];
-    float4 *LT = (float4 *)smem;                                 // [128]      df64 log table
-    float *RS = (float *)(smem + SM::lt());                      // [4][NC][kT] rho hi rows
-    float *RL = (float *)(smem + SM::lt() + SM::rs(W));          // [4][NC][kT] rho lo rows
-    ET *PS = (ET *)(smem + SM::lt() + 2 * SM::rs(W));            // [3][kT]     psi rows
+    float *RS = (float *)smem;                                   // [4][NC][kT] rho hi rows
+    float *RL = (float *)(smem + SM::rs(W));                     // [4][NC][kT] rho lo rows
+    float *PS = (float *)(smem + 2 * SM::rs(W));                 // [3][kT]     psi rows (binary32 only)
     ET *MU = (ET *)((unsigned char *)PS + SM::ps(W));            // [3][NC][kT] mu rows
-    float *XC = (float *)((unsigned char *)MU + SM::mu(W));      // [4][NC][kT] exchange
-    float *BND = (float *)((unsigned char *)XC + SM::xc());      // [kT/32][2][NC] warp edges
-    double *RED = (double *)((unsigned char *)BND + SM::bnd());
+    float *XC = (float *)((unsigned char *)MU + SM::mu(W));      // [6][NC][kT] exchange
+    double *RED = (double *)((unsigned char *)XC + SM::xc());
     float *MS = (float *)((unsigned char *)RED + SM::red());     // [2][NC][kT] mass of rows written
     const float *gin = (const float *)in.g;
     float *gout = (float *)out.g;
@@ -410,21 +475,21 @@ __global__ void __launch_bounds__(kT)
     const int y0 = blockIdx.y * H;
     const int h = min(H, ny - y0);
     const int t = threadIdx.x;
-    const int lane = t & 31, warp = t >> 5;
     const int col = t - 1;
     const bool active = t < w + 2;
     const bool interior = col >= 0 && col < w;
-    const unsigned amask = __ballot_sync(0xffffffffu, active);
     const int xg = wrapc(x0 + col, nx);
     const int xd[3] = {wrapc(xg - 1, nx), xg, wrapc(xg + 1, nx)};
     // phase (A): one density column per thread (strips are at most kT - 6 wide)
     const int cA0 = t - 3;
     const bool hasA0 = cA0 < w + 3;
     const int xA0 = wrapc(x0 + cA0, nx);
+    // phase (B), double-binary32: mu column of this thread, -2 .. w + 1
+    const int cB = t - 2;
+    const bool hasB = cB < w + 2;
+    const int xB = wrapc(x0 + cB, nx);
     const float om = (float)P.omega, om1 = (float)(1.0 - P.omega), cF = (float)(1.0 - 0.5 * P.omega);
 
-    if constexpr (kDF)
-        for (int j = t; j < df::kLogTab; j += kT) LT[j] = P.logtab[j];
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
         MS[(0 * NC + i) * kT + t] = 0.0f;
@@ -447,7 +512,7 @@ __global__ void __launch_bounds__(kT)
     for (int kk = 0; kk < nrows; ++kk) {
         const int k = y0 - 3 + kk;
         const int crow = k - 2;
-        // ---- (A) density pair and psi of row k ----------------------------------
+        // ---- (A) density pair (and binary32 psi) of row k --------------------------
         {
             const int s4 = kk & 3, s3 = kk % 3;
             if (hasA0) {
@@ -456,43 +521,34 @@ __global__ void __launch_bounds__(kT)
                     RS[(s4 * NC + i) * CW + cA0 + 3] = rh0[i];
                     RL[(s4 * NC + i) * CW + cA0 + 3] = rl0[i];
                 }
-                if constexpr (kDF) {
-                    const df::F2 ps = df::psi<NC>(P, rh0, rl0);
-                    PS[s3 * CW + cA0 + 3] = make_float2(ps.hi, ps.lo);
-                } else {
+                if constexpr (!kDF) {
                     float ps = 0.0f;
 #pragma unroll
                     for (int i = 0; i < NC; ++i) ps = fmaf(VF::sqk(P, i), (rh0[i] + rl0[i]) * VF::invM(P, i), ps);
                     PS[s3 * CW + cA0 + 3] = ps;
                 }
             }
+            // ---- (B) double-binary32: mu of row k-1, computed by k_mu32 ----------
+            if constexpr (kDF) {
+                if (kk >= 2 && hasB) {
+                    const int q = kk - 1;
+                    const IDX rb = (IDX)wrapc(k - 1, ny) * (IDX)nx + (IDX)xB;
+#pragma unroll
+                    for (int i = 0; i < NC; ++i) MU[((q % 3) * NC + i) * CM + cB + 2] = __ldg(mug + i * N + rb);
+                }
+            }
         }
         __syncthreads();
-        // ---- (B) ln f and mu of row k-1 ------------------------------------------
-        if (kk >= 2) {
-            const int q = kk - 1;
-            const int s4 = q & 3;
-            const ET *p0 = PS + ((q + 2) % 3) * CW;
-            const ET *p1 = PS + (q % 3) * CW;
-            const ET *p2 = PS + ((q + 1) % 3) * CW;
-            for (int c = t - 2; c < w + 2; c += kT) {
-                const int cc = c + 3;
-                if constexpr (kDF) {
-                    float hh[NC], ll[NC];
-#pragma unroll
-                    for (int i = 0; i < NC; ++i) {
-                        hh[i] = RS[(s4 * NC + i) * CW + cc];
-                        ll[i] = RL[(s4 * NC + i) * CW + cc];
-                    }
-                    const df::F2 lap = df::lap9(df::f2(p1[cc]), df::f2(p1[cc + 1]), df::f2(p1[cc - 1]),
-                                                df::f2(p2[cc]), df::f2(p0[cc]), df::f2(p2[cc + 1]),
-                                                df::f2(p2[cc - 1]), df::f2(p0[cc + 1]), df::f2(p0[cc - 1]));
-                    df::F2 mu[NC];
-                    df::mu<NC>(P, LT, hh, ll, lap, mu);
-#pragma unroll
-                    for (int i = 0; i < NC; ++i)
-                        MU[((q % 3) * NC + i) * CM + c + 2] = make_float2(mu[i].hi, mu[i].lo);
-                } else {
+        // ---- (B) binary32: ln f and mu of row k-1 ----------------------------------
+        if constexpr (!kDF) {
+            if (kk >= 2) {
+                const int q = kk - 1;
+                const int s4 = q & 3;
+                const float *p0 = PS + ((q + 2) % 3) * CW;
+                const float *p1 = PS + (q % 3) * CW;
+                const float *p2 = PS + ((q + 1) % 3) * CW;
+                for (int c = t - 2; c < w + 2; c += kT) {
+                    const int cc = c + 3;
                     float rm[NC], lf[NC];
 #pragma unroll
                     for (int i = 0; i < NC; ++i)
@@ -508,8 +564,8 @@ __global__ void __launch_bounds__(kT)
                         MU[((q % 3) * NC + i) * CM + c + 2] = fmaf(RT, lf[i], -VF::sqk(P, i) * lap);
                 }
             }
+            __syncthreads();
         }
-        __syncthreads();
         // density pair of row k+1 for phase (A) of the next row: issued here
         // before the first collision row, in the density update after it
         const IDX rowb1 = (IDX)wrapc(k + 1, ny) * (IDX)nx + (IDX)xA0;
@@ -555,8 +611,8 @@ __global__ void __launch_bounds__(kT)
                 jy += (v[2] - v[3]) + (v[4] - v[5]) + (v[7] - v[6]);
             }
             // Eq. (5): F_i = -rho~_i grad mu_i.  grad X = 3 sum_pairs w e (X(r+e) - X(r-e));
-            // with df64 mu every difference is taken on the (hi, lo) pairs and
-            // rounded once, so it carries the df64 accuracy of mu.
+            // with double-binary32 mu every difference is taken on the (hi, lo)
+            // pairs and rounded once, so it carries the df64 accuracy of mu.
             float Fx[NC], Fy[NC], rlo1[NC];
             float Fsx = 0.0f, Fsy = 0.0f, rt = 0.0f;
 #pragma unroll
@@ -645,20 +701,9 @@ __global__ void __launch_bounds__(kT)
                         if (bx == 0) {
                             if (by < 0) own0[i] = gs;
                             else own2[i] = gs;
-                        } else if (by != 0) {
-                            XC[((((by + 1) >> 1) * 2 + (bx > 0 ? 0 : 1)) * NC + i) * kT + t] = gs;
+                        } else {
+                            XC[(((by + 1) * 2 + (bx > 0 ? 0 : 1)) * NC + i) * kT + t] = gs;
                         }
-                    }
-                    if (ey == 0) {
-                        // same-row arrivals: the left neighbour's +x value and the
-                        // right neighbour's -x value, by shuffle within the warp;
-                        // the warp's edge lanes take theirs from BND after the barrier
-                        const float fromL = __shfl_up_sync(amask, gp, 1);
-                        const float fromR = __shfl_down_sync(amask, gm, 1);
-                        if (lane == 31) BND[(warp * 2 + 0) * NC + i] = gp;
-                        if (lane == 0) BND[(warp * 2 + 1) * NC + i] = gm;
-                        if (lane > 0) pair_acc(bH[i], bL[i], fromL);
-                        if (lane < 31) pair_acc(bH[i], bL[i], fromR);
                     }
                 }
             }
@@ -694,18 +739,17 @@ __global__ void __launch_bounds__(kT)
                     MS[(0 * NC + i) * kT + t] = ms;
                     MS[(1 * NC + i) * kT + t] = mc + lo;
                 }
-                // row crow (its departures and in-warp same-row arrivals were
-                // applied during the collision): the edge lanes' arrivals
+                // row crow (its departures left during the collision): arrivals along the row
                 aH[i] = bH[i];
                 aL[i] = bL[i];
-                if (lane == 0) pair_acc(aH[i], aL[i], BND[((warp - 1) * 2 + 0) * NC + i]);
-                if (lane == 31) pair_acc(aH[i], aL[i], BND[((warp + 1) * 2 + 1) * NC + i]);
+                pair_acc(aH[i], aL[i], xc[2 * NC * kT + t - 1]);
+                pair_acc(aH[i], aL[i], xc[3 * NC * kT + t + 1]);
                 // row crow+1: its old density, then the first arrivals
                 bH[i] = Rh2[i * CW + cc];
                 bL[i] = RL[(((q + 1) & 3) * NC + i) * CW + cc];
-                pair_acc(bH[i], bL[i], xc[2 * NC * kT + t - 1]);
+                pair_acc(bH[i], bL[i], xc[4 * NC * kT + t - 1]);
                 pair_acc(bH[i], bL[i], own2[i]);
-                pair_acc(bH[i], bL[i], xc[3 * NC * kT + t + 1]);
+                pair_acc(bH[i], bL[i], xc[5 * NC * kT + t + 1]);
             }
         }
     }
@@ -746,15 +790,20 @@ __global__ void k_density(const Params P, const S *__restrict__ g, S *__restrict
 struct Ops {
     int wmax;
     int (*density)(const Params &, StateBufs, cudaStream_t);
-    int (*step)(const Params &, const FusedGeom &, StateBufs, StateBufs, double *, cudaStream_t);
+    // one step; mu: the double-binary32 chemical-potential buffer [nc][N]
+    // (LBM_FP32DEV), else unused.  Returns the launches made through *launches.
+    int (*step)(const Params &, const FusedGeom &, StateBufs, StateBufs, double *, float2 *mu, int *launches,
+                cudaStream_t);
     size_t (*smem)(int W);
     int (*occupancy)(size_t smem);
+    int (*occupancy_mu)();  // CTAs per SM of the mu pass (0: the form has none)
 };
 
 // S = double: binary64 kernel (all populations, binary64 densities).
-// S = float:  binary32 kernel with thermodynamics in E.
+// S = float:  binary32 kernel with thermodynamics in E (DF64: a mu pass first).
 template <int NC, typename S, typename E> struct Impl {
     static constexpr bool k64 = sizeof(S) == 8;
+    static constexpr bool kDF = std::is_same<E, DF64>::value;
     static auto kernel()
     {
         if constexpr (k64) return k_fused<NC, double, double>;
@@ -791,26 +840,51 @@ template <int NC, typename S, typename E> struct Impl {
             return 0;
         return n;
     }
-    static int step(const Params &P, const FusedGeom &g, StateBufs in, StateBufs out, double *mp,
-                    cudaStream_t s)
+    static int occupancy_mu()
+    {
+        if constexpr (kDF) {
+            int n = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mu32<NC, long long>, kT, 0) != cudaSuccess)
+                return 0;
+            return n;
+        } else {
+            return 0;
+        }
+    }
+    static int step(const Params &P, const FusedGeom &g, StateBufs in, StateBufs out, double *mp, float2 *mu,
+                    int *launches, cudaStream_t s)
     {
         dim3 grid(g.nstrips, g.segs);
-        if constexpr (k64)
+        const bool small = (long long)NC * 8 * P.N < (1LL << 31);
+        *launches = 1;
+        if constexpr (k64) {
             k_fused<NC, double, double><<<grid, kT, g.smem, s>>>(
                 P, g.strip, g.seg_h, (const double *)in.g, (double *)out.g, in.rhi_d(),
                 out.rhi_d(), mp);
-        else if ((long long)NC * 8 * P.N < (1LL << 31))
-            k_fused32<NC, E, int><<<grid, kT, g.smem, s>>>(P, g.strip, g.seg_h, in, out, mp);
-        else
-            k_fused32<NC, E, long long><<<grid, kT, g.smem, s>>>(P, g.strip, g.seg_h, in, out, mp);
+        } else {
+            if constexpr (kDF) {
+                if (!mu) return (int)cudaErrorInvalidValue;
+                dim3 mgrid(g.mnstrips, g.msegs);
+                if (small)
+                    k_mu32<NC, int><<<mgrid, kT, 0, s>>>(P, g.mstrip, g.mseg_h, in, mu);
+                else
+                    k_mu32<NC, long long><<<mgrid, kT, 0, s>>>(P, g.mstrip, g.mseg_h, in, mu);
+                *launches = 2;
+            }
+            if (small)
+                k_fused32<NC, E, int><<<grid, kT, g.smem, s>>>(P, g.strip, g.seg_h, in, out, mp, mu);
+            else
+                k_fused32<NC, E, long long><<<grid, kT, g.smem, s>>>(P, g.strip, g.seg_h, in, out, mp, mu);
+        }
         return (int)cudaGetLastError();
     }
 };
 
 template <int NC, typename S, typename E> const Ops *ops_of()
 {
-    static const Ops o = {Impl<NC, S, E>::wmax(), &Impl<NC, S, E>::density, &Impl<NC, S, E>::step,
-                          &Impl<NC, S, E>::smem, &Impl<NC, S, E>::occupancy};
+    static const Ops o = {Impl<NC, S, E>::wmax(),     &Impl<NC, S, E>::density,
+                          &Impl<NC, S, E>::step,      &Impl<NC, S, E>::smem,
+                          &Impl<NC, S, E>::occupancy, &Impl<NC, S, E>::occupancy_mu};
     return &o;
 }
 

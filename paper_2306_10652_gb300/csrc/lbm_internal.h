@@ -40,6 +40,8 @@ struct FusedGeom {
     int seg_h;    // rows per CTA
     int threads;  // threads per CTA
     size_t smem;  // dynamic shared memory bytes
+    // the chemical-potential pass of LBM_FP32DEV (0 for the other forms)
+    int mstrip, mnstrips, msegs, mseg_h;
 };
 
 // All launchers return a cudaError_t cast to int (0 = success).
@@ -67,8 +69,10 @@ bool fused_supported(int lat, int prec, int nc);
 FusedGeom fused_geometry(int prec, int nc, const Params &P, int num_sms);
 // binary64 only: densities of the fused state from the populations
 int launch_fused_density(int prec, int nc, const Params &P, StateBufs st, cudaStream_t s);
+// mu: [nc][N] (hi, lo) chemical potentials of LBM_FP32DEV (else unused);
+// *launches receives the kernels launched.
 int launch_fused_step(int prec, int nc, const Params &P, const FusedGeom &geo, StateBufs in,
-                      StateBufs out, double *mass_partials, cudaStream_t s);
+                      StateBufs out, double *mass_partials, float2 *mu, int *launches, cudaStream_t s);
 // Sum the per-CTA mass partials of a monitored fused step into out[nc].
 int launch_fused_mass_final(int nc, const FusedGeom &geo, const double *partials, double *out,
                             int *nonfinite, cudaStream_t s);
