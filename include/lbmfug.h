@@ -267,7 +267,8 @@ int lbm_batch_create(lbm_batch **out, int Nc, const double *a, const double *b, 
  * ulp being the spacing of binary32 numbers at the problem's largest
  * density (the stored populations are binary32, and below that their
  * rounding, not relaxation, moves the densities), or when a density is not
- * finite (failed; it is retired and the others go on).
+ * finite (failed; it is retired and the others go on).  tol = 0 runs every
+ * problem to max_steps.
  * *n_converged receives the number of finished problems.  Synchronises. */
 int lbm_batch_run(lbm_batch *b, long long max_steps, int check_every, double tol, int *n_converged);
 
@@ -295,8 +296,8 @@ int lbm_batch_destroy(lbm_batch *b);
  * than max_active jobs run; every running job is its own problem on its own
  * stream, advanced in rounds of check_every steps whose kernels overlap on
  * the GPU; a job finishes when the largest density change over a round is
- * below tol (converged; with binary32 storage below max(tol, 8 ulp of
- * binary32 at 1.05 times its largest initial density)), when a density is
+ * below tol (converged; with binary32 storage and tol > 0 below max(tol,
+ * 8 ulp of binary32 at 1.05 times its largest initial density)), when a density is
  * not finite (failed) or after
  * max_steps steps (exhausted), and its memory goes to the next request.
  * ------------------------------------------------------------------------ */

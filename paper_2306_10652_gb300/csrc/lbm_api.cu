@@ -38,7 +38,7 @@ struct lbm_problem {
     double *snap = nullptr;
     bool have_snap = false;
     void *fscratch = nullptr;  // psi / mu scratch of lbm_forces
-    float2 *mu = nullptr;      // [nc][N] chemical potentials of the LBM_FP32DEV step
+    float2 *mu = nullptr;      // [nc][N] grad mu_i of the LBM_FP32DEV step (the mu pass writes it)
     long long launches = 0;
     long long monitor_step = -1;
     double *mon = nullptr;  // [nc] latest monitored mass
@@ -133,6 +133,11 @@ void refresh_float_params(Params &P)
             P.dA[i * kMaxNc + j] = split2(P.A[i * kMaxNc + j] * invMj);
         }
     }
+    for (int r = 0; r < kMaxNc / 2; ++r)
+        for (int j = 0; j < kMaxNc; ++j) {
+            const float2 a = P.dA[(2 * r) * kMaxNc + j], b = P.dA[(2 * r + 1) * kMaxNc + j];
+            P.dAp[r * kMaxNc + j] = make_float4(a.x, b.x, a.y, b.y);
+        }
     P.dRT = split2(P.RT);
     df::make_log_table(&P.logtab[0].x);
 }
@@ -224,7 +229,7 @@ int ensure_allocated(lbm_problem *p)
             (double *)dev_alloc(p, (size_t)p->geo.nstrips * p->geo.segs * p->nc * sizeof(double));
         if (!p->mass_partials || p->geo.nstrips < 1) return LBM_ENOMEM;
         if (p->opt.precision == LBM_FP32DEV) {
-            p->mu = (float2 *)dev_alloc(p, nf * sizeof(float2));
+            p->mu = (float2 *)dev_alloc(p, nf * sizeof(float2));  // grad mu_i, written by the mu pass
             if (!p->mu || p->geo.mnstrips < 1) return LBM_ENOMEM;
         }
     }

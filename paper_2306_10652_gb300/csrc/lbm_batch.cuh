@@ -280,7 +280,7 @@ __global__ void k_batch_round(const Shared S, const Job *__restrict__ jobs, Stat
             }
             // the stored populations are binary32: below 8 ulp of the largest
             // density a change is their rounding jitter, not relaxation
-            const double bar = fmax(tol, 8.0 * ulp32(r));
+            const double bar = tol > 0.0 ? fmax(tol, 8.0 * ulp32(r)) : 0.0;  // tol = 0: run to the step cap
             Status &st = status[jid];
             st.cur = cur;
             st.steps += steps;

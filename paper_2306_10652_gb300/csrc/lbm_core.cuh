@@ -78,6 +78,7 @@ struct Params {
     float2 dB[kMaxNc];           // b_i / M_i
     float2 db[kMaxNc];           // b_i
     float2 dA[kMaxNc * kMaxNc];  // A_ij / M_j
+    float4 dAp[kMaxNc / 2 * kMaxNc];  // rows 2r, 2r+1 side by side: (hi_2r, hi_2r+1, lo_2r, lo_2r+1) at column j
     float2 dRK[kMaxNc];          // RT (ln RT - ln M_i)
     float2 dsqk[kMaxNc];         // sqrt(kappa_i)
     float2 dPk[kMaxNc];          // sqrt(kappa_j) / M_j

@@ -349,7 +349,7 @@ template <int NC, typename E> struct Smem32 {
     static constexpr bool kDF = sizeof(ET) == 8;
     static __host__ __device__ constexpr size_t rs(int) { return align16((size_t)4 * NC * kT * sizeof(float)); }
     static __host__ __device__ constexpr size_t ps(int) { return kDF ? 0 : align16((size_t)3 * kT * sizeof(float)); }
-    static __host__ __device__ constexpr size_t mu(int) { return align16((size_t)3 * NC * kT * sizeof(ET)); }
+    static __host__ __device__ constexpr size_t mu(int) { return kDF ? 0 : align16((size_t)3 * NC * kT * sizeof(ET)); }
     static __host__ __device__ constexpr size_t xc() { return align16((size_t)6 * NC * kT * sizeof(float)); }
     static __host__ __device__ constexpr size_t red() { return align16((size_t)(kT / 32) * NC * sizeof(double)); }
     static __host__ __device__ constexpr size_t ms() { return align16((size_t)2 * NC * kT * sizeof(float)); }
@@ -359,23 +359,37 @@ template <int NC, typename E> struct Smem32 {
     }
 };
 constexpr int kWmax32 = kT - 6;  // binary32 kernel: one density column per thread
-constexpr int kWmaxMu = kT - 2;  // mu pass: psi on one halo column each side
 
-// Double-binary32 chemical potentials (LBM_FP32DEV), one pass before the step
-// kernel.  Each CTA walks a segment of rows of a strip of W <= kT - 2
-// columns: for row k it forms psi(k) (Eq. 4) on columns [-1, W] from the
-// state's exact density pairs, then mu of row k-1 (Eqs. 5, 9-12 through
-// lbm_thermo_df.cuh) on the interior columns from psi rows k-2..k and the
-// pairs of row k-1 it kept from the previous row, and writes it to
-// mu[i][node] as (hi, lo).  psi rows live in a ring of four, so one barrier
-// per row suffices (a row's slot is rewritten only after every thread has
-// passed the barrier that follows its last reader).
+// Double-binary32 chemical potentials and their gradients (LBM_FP32DEV), one
+// pass before the step kernel.  Each CTA walks a segment of rows of a strip
+// of W <= kT - 4 columns; for row k it forms
+//   psi(k) (Eq. 4) on columns [-2, W + 1] from the state's exact density pairs,
+//   mu(k-1) (Eqs. 5, 9-12 through lbm_thermo_df.cuh) on columns [-1, W] from
+//     psi rows k-2..k and the pairs of row k-1 kept from the previous row,
+//   grad mu(k-2) on the interior columns from mu rows k-3..k-1, every
+//     difference mu(r + e) - mu(r - e) taken on the (hi, lo) pairs and
+//     rounded once (so it carries the df64 accuracy of mu), written to
+//     G[i][node] = (d mu_i / dx, d mu_i / dy) in binary32.
+// The step kernel forms F_i = -rho~_i G_i.  psi rows live in a ring of four
+// and mu rows in a ring of three: a slot is rewritten only after the barrier
+// that follows its last reader.
+constexpr int kWmaxMu = kT - 4;
+
+template <int NC> struct SmemMu {
+    static __host__ __device__ constexpr size_t bytes()
+    {
+        return (size_t)df::kLogTab * sizeof(float4) + 4 * kT * sizeof(float2) + 3 * NC * kT * sizeof(float2);
+    }
+};
+
 template <int NC, typename IDX>
 __global__ void __launch_bounds__(kT) k_mu32(const Params P, const int W, const int H, StateBufs in,
-                                             float2 *__restrict__ mug)
+                                             float2 *__restrict__ G)
 {
-    __shared__ float4 LT[df::kLogTab];
-    __shared__ float2 PS[4][kT];
+    extern __shared__ __align__(16) unsigned char smem[];
+    float4 *LT = (float4 *)smem;                                           // [128]
+    float2 *PS = (float2 *)(smem + df::kLogTab * sizeof(float4));          // [4][kT]
+    float2 *MU = PS + 4 * kT;                                              // [3][NC][kT]
     const int nx = P.nx, ny = P.ny;
     const IDX N = (IDX)P.N;
     const int x0 = blockIdx.x * W;
@@ -383,8 +397,9 @@ __global__ void __launch_bounds__(kT) k_mu32(const Params P, const int W, const 
     const int y0 = blockIdx.y * H;
     const int h = min(H, ny - y0);
     const int t = threadIdx.x;
-    const int c = t - 1;  // column of this thread, -1 .. w
-    const bool has = c <= w;
+    const int c = t - 2;  // column of this thread, -2 .. w + 1
+    const bool hasP = c <= w + 1;
+    const bool hasM = c >= -1 && c <= w;
     const bool interior = c >= 0 && c < w;
     const int xg = wrapc(x0 + c, nx);
     const float *rhin = in.rhi_f();
@@ -393,10 +408,10 @@ __global__ void __launch_bounds__(kT) k_mu32(const Params P, const int W, const 
     float ph[NC], pl[NC];  // density pairs of row k-1 at this column
 #pragma unroll
     for (int i = 0; i < NC; ++i) ph[i] = pl[i] = 0.0f;
-    for (int kk = 0; kk < h + 2; ++kk) {
-        const int k = y0 - 1 + kk;
+    for (int kk = 0; kk < h + 4; ++kk) {
+        const int k = y0 - 2 + kk;
         float hh[NC], ll[NC];
-        if (has) {
+        if (hasP) {
             const IDX rb = (IDX)wrapc(k, ny) * (IDX)nx + (IDX)xg;
 #pragma unroll
             for (int i = 0; i < NC; ++i) {
@@ -404,25 +419,45 @@ __global__ void __launch_bounds__(kT) k_mu32(const Params P, const int W, const 
                 ll[i] = __ldg(rlin + i * N + rb);
             }
             const df::F2 ps = df::psi<NC>(P, hh, ll);
-            PS[kk & 3][t] = make_float2(ps.hi, ps.lo);
+            PS[(kk & 3) * kT + t] = make_float2(ps.hi, ps.lo);
         }
         __syncthreads();
-        if (kk >= 2 && interior) {
-            const float2 *p0 = PS[(kk - 2) & 3], *p1 = PS[(kk - 1) & 3], *p2 = PS[kk & 3];
+        if (kk >= 2 && kk < h + 4 && hasM) {
+            const float2 *p0 = PS + ((kk - 2) & 3) * kT, *p1 = PS + ((kk - 1) & 3) * kT, *p2 = PS + (kk & 3) * kT;
             const df::F2 lap = df::lap9(df::f2(p1[t]), df::f2(p1[t + 1]), df::f2(p1[t - 1]), df::f2(p2[t]),
                                         df::f2(p0[t]), df::f2(p2[t + 1]), df::f2(p2[t - 1]), df::f2(p0[t + 1]),
                                         df::f2(p0[t - 1]));
             df::F2 m[NC];
             df::mu<NC>(P, LT, ph, pl, lap, m);
-            const IDX ob = (IDX)wrapc(k - 1, ny) * (IDX)nx + (IDX)xg;
 #pragma unroll
-            for (int i = 0; i < NC; ++i) mug[i * N + ob] = make_float2(m[i].hi, m[i].lo);
+            for (int i = 0; i < NC; ++i) MU[(((kk - 1) % 3) * NC + i) * kT + t] = make_float2(m[i].hi, m[i].lo);
         }
-        if (has) {
+        if (hasP) {
 #pragma unroll
             for (int i = 0; i < NC; ++i) {
                 ph[i] = hh[i];
                 pl[i] = ll[i];
+            }
+        }
+        __syncthreads();
+        if (kk >= 4 && interior) {
+            // gradient of mu at row k-2: rows k-3 (south), k-2, k-1 (north)
+            const float2 *S = MU + ((kk - 3) % 3) * NC * kT, *C = MU + ((kk - 2) % 3) * NC * kT,
+                         *Nr = MU + ((kk - 1) % 3) * NC * kT;
+            const IDX ob = (IDX)wrapc(k - 2, ny) * (IDX)nx + (IDX)xg;
+#pragma unroll
+            for (int i = 0; i < NC; ++i) {
+                const float2 *s0 = S + i * kT, *c0 = C + i * kT, *n0 = Nr + i * kT;
+                const float2 e1 = c0[t + 1], w1 = c0[t - 1], n1 = n0[t], s1 = s0[t];
+                const float2 ne = n0[t + 1], sw = s0[t - 1], se = s0[t + 1], nw = n0[t - 1];
+                const float dE = (e1.x - w1.x) + (e1.y - w1.y);
+                const float dN = (n1.x - s1.x) + (n1.y - s1.y);
+                const float dNE = (ne.x - sw.x) + (ne.y - sw.y);
+                const float dSE = (se.x - nw.x) + (se.y - nw.y);
+                // grad X = 3 sum_pairs w e (X(r+e) - X(r-e)): faces 1/9, diagonals 1/36
+                const float gx = 3.0f * fmaf(1.0f / 9.0f, dE, (1.0f / 36.0f) * (dNE + dSE));
+                const float gy = 3.0f * fmaf(1.0f / 9.0f, dN, (1.0f / 36.0f) * (dNE - dSE));
+                G[i * N + ob] = make_float2(gx, gy);
             }
         }
     }
@@ -447,7 +482,7 @@ __device__ __forceinline__ void pair_acc(float &hi, float &lo, float x)
 template <int NC, typename E, typename IDX>
 __global__ void __launch_bounds__(kT)
     k_fused32(const Params P, const int W, const int H, StateBufs in, StateBufs out,
-              double *__restrict__ mass_partials, const float2 *__restrict__ mug)
+              double *__restrict__ mass_partials, const float2 *__restrict__ mug /* grad mu, DF64 */)
 {
     using L = Lattice<0>;
     using SM = Smem32<NC, E>;
@@ -484,10 +519,6 @@ __global__ void __launch_bounds__(kT)
     const int cA0 = t - 3;
     const bool hasA0 = cA0 < w + 3;
     const int xA0 = wrapc(x0 + cA0, nx);
-    // phase (B), double-binary32: mu column of this thread, -2 .. w + 1
-    const int cB = t - 2;
-    const bool hasB = cB < w + 2;
-    const int xB = wrapc(x0 + cB, nx);
     const float om = (float)P.omega, om1 = (float)(1.0 - P.omega), cF = (float)(1.0 - 0.5 * P.omega);
 
 #pragma unroll
@@ -526,15 +557,6 @@ __global__ void __launch_bounds__(kT)
 #pragma unroll
                     for (int i = 0; i < NC; ++i) ps = fmaf(VF::sqk(P, i), (rh0[i] + rl0[i]) * VF::invM(P, i), ps);
                     PS[s3 * CW + cA0 + 3] = ps;
-                }
-            }
-            // ---- (B) double-binary32: mu of row k-1, computed by k_mu32 ----------
-            if constexpr (kDF) {
-                if (kk >= 2 && hasB) {
-                    const int q = kk - 1;
-                    const IDX rb = (IDX)wrapc(k - 1, ny) * (IDX)nx + (IDX)xB;
-#pragma unroll
-                    for (int i = 0; i < NC; ++i) MU[((q % 3) * NC + i) * CM + cB + 2] = __ldg(mug + i * N + rb);
                 }
             }
         }
@@ -599,10 +621,13 @@ __global__ void __launch_bounds__(kT)
             const ET *M2 = MU + ((q + 1) % 3) * NC * CM;
             const IDX rc = (IDX)yc * (IDX)nx + (IDX)xg;
             float hv[NC][8];
+            float2 gm[kDF ? NC : 1];  // double-binary32: grad mu_i from k_mu32
 #pragma unroll
-            for (int i = 0; i < NC; ++i)
+            for (int i = 0; i < NC; ++i) {
 #pragma unroll
                 for (int a = 0; a < 8; ++a) hv[i][a] = __ldg(gin + (i * 8 + a) * N + rc);
+                if constexpr (kDF) gm[i] = __ldg(mug + i * N + rc);
+            }
             float jx = 0.0f, jy = 0.0f;
 #pragma unroll
             for (int i = 0; i < NC; ++i) {
@@ -610,30 +635,25 @@ __global__ void __launch_bounds__(kT)
                 jx += (v[0] - v[1]) + (v[4] - v[5]) + (v[6] - v[7]);
                 jy += (v[2] - v[3]) + (v[4] - v[5]) + (v[7] - v[6]);
             }
-            // Eq. (5): F_i = -rho~_i grad mu_i.  grad X = 3 sum_pairs w e (X(r+e) - X(r-e));
-            // with double-binary32 mu every difference is taken on the (hi, lo)
-            // pairs and rounded once, so it carries the df64 accuracy of mu.
+            // Eq. (5): F_i = -rho~_i grad mu_i, grad X = 3 sum_pairs w e (X(r+e) - X(r-e));
+            // double-binary32: the gradient comes from k_mu32
             float Fx[NC], Fy[NC], rlo1[NC];
             float Fsx = 0.0f, Fsy = 0.0f, rt = 0.0f;
 #pragma unroll
             for (int i = 0; i < NC; ++i) {
-                const ET *m0 = M0 + i * CM, *m1 = M1 + i * CM, *m2 = M2 + i * CM;
-                float dE, dN, dNE, dSE;
+                float gx, gy;
                 if constexpr (kDF) {
-                    const float2 e1 = m1[cm + 1], w1 = m1[cm - 1], n1 = m2[cm], s1 = m0[cm];
-                    const float2 ne = m2[cm + 1], sw = m0[cm - 1], se = m0[cm + 1], nw = m2[cm - 1];
-                    dE = (e1.x - w1.x) + (e1.y - w1.y);
-                    dN = (n1.x - s1.x) + (n1.y - s1.y);
-                    dNE = (ne.x - sw.x) + (ne.y - sw.y);
-                    dSE = (se.x - nw.x) + (se.y - nw.y);
+                    gx = gm[i].x;
+                    gy = gm[i].y;
                 } else {
-                    dE = m1[cm + 1] - m1[cm - 1];
-                    dN = m2[cm] - m0[cm];
-                    dNE = m2[cm + 1] - m0[cm - 1];
-                    dSE = m0[cm + 1] - m2[cm - 1];
+                    const ET *m0 = M0 + i * CM, *m1 = M1 + i * CM, *m2 = M2 + i * CM;
+                    const float dE = m1[cm + 1] - m1[cm - 1];
+                    const float dN = m2[cm] - m0[cm];
+                    const float dNE = m2[cm + 1] - m0[cm - 1];
+                    const float dSE = m0[cm + 1] - m2[cm - 1];
+                    gx = 3.0f * fmaf(1.0f / 9.0f, dE, (1.0f / 36.0f) * (dNE + dSE));
+                    gy = 3.0f * fmaf(1.0f / 9.0f, dN, (1.0f / 36.0f) * (dNE - dSE));
                 }
-                const float gx = 3.0f * fmaf(1.0f / 9.0f, dE, (1.0f / 36.0f) * (dNE + dSE));
-                const float gy = 3.0f * fmaf(1.0f / 9.0f, dN, (1.0f / 36.0f) * (dNE - dSE));
                 rlo1[i] = RL[((q & 3) * NC + i) * CW + cc];
                 const float ri = R1[i * CW + cc] + rlo1[i];
                 rt += ri;
@@ -790,8 +810,8 @@ __global__ void k_density(const Params P, const S *__restrict__ g, S *__restrict
 struct Ops {
     int wmax;
     int (*density)(const Params &, StateBufs, cudaStream_t);
-    // one step; mu: the double-binary32 chemical-potential buffer [nc][N]
-    // (LBM_FP32DEV), else unused.  Returns the launches made through *launches.
+    // one step; mu: the gradient buffer of the double-binary32 chemical
+    // potentials, [nc][N] (d/dx, d/dy) (LBM_FP32DEV), else unused.  Returns the launches made through *launches.
     int (*step)(const Params &, const FusedGeom &, StateBufs, StateBufs, double *, float2 *mu, int *launches,
                 cudaStream_t);
     size_t (*smem)(int W);
@@ -843,8 +863,14 @@ template <int NC, typename S, typename E> struct Impl {
     static int occupancy_mu()
     {
         if constexpr (kDF) {
+            const size_t b = SmemMu<NC>::bytes();
+            if (cudaFuncSetAttribute(k_mu32<NC, long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b) !=
+                    cudaSuccess ||
+                cudaFuncSetAttribute(k_mu32<NC, int>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b) !=
+                    cudaSuccess)
+                return 0;
             int n = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mu32<NC, long long>, kT, 0) != cudaSuccess)
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mu32<NC, long long>, kT, b) != cudaSuccess)
                 return 0;
             return n;
         } else {
@@ -865,10 +891,11 @@ template <int NC, typename S, typename E> struct Impl {
             if constexpr (kDF) {
                 if (!mu) return (int)cudaErrorInvalidValue;
                 dim3 mgrid(g.mnstrips, g.msegs);
+                const size_t b = SmemMu<NC>::bytes();
                 if (small)
-                    k_mu32<NC, int><<<mgrid, kT, 0, s>>>(P, g.mstrip, g.mseg_h, in, mu);
+                    k_mu32<NC, int><<<mgrid, kT, b, s>>>(P, g.mstrip, g.mseg_h, in, mu);
                 else
-                    k_mu32<NC, long long><<<mgrid, kT, 0, s>>>(P, g.mstrip, g.mseg_h, in, mu);
+                    k_mu32<NC, long long><<<mgrid, kT, b, s>>>(P, g.mstrip, g.mseg_h, in, mu);
                 *launches = 2;
             }
             if (small)

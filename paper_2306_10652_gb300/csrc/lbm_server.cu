@@ -124,7 +124,7 @@ struct lbm_server {
         // binary32 storage jitters at the rounding of its populations: changes
         // below 8 ulp of binary32 at the largest density count as converged
         r->bar = r->tol;
-        if (r->precision != LBM_FP64) {
+        if (r->precision != LBM_FP64 && r->tol > 0.0) {
             double rmax = 0.0;
             for (double v : r->rho) rmax = std::max(rmax, v);
             int e = 0;

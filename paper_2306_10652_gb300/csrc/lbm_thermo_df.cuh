@@ -39,6 +39,37 @@ __device__ __forceinline__ F2 mul_u(F2 a, F2 b)
     return {p.hi, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo))};
 }
 
+// Two compensated dot products at once on the packed FP32x2 units: the
+// lanes are rows 2r and 2r+1 of T_i = sum_j (A_ij / M_j) rho_j, with the
+// same TwoProd / TwoSum steps as Dot, so each lane equals Dot's result.
+__device__ __forceinline__ float2 pneg(float2 a) { return make_float2(-a.x, -a.y); }
+
+struct Dot2x {
+    float2 s, c;
+    __device__ __forceinline__ void first(float4 A, float xh, float xl)
+    {
+        const float2 X = make_float2(xh, xh), XL = make_float2(xl, xl);
+        const float2 ch = make_float2(A.x, A.y), cl = make_float2(A.z, A.w);
+        const float2 p = __fmul2_rn(ch, X);
+        const float2 pe = __ffma2_rn(ch, X, pneg(p));
+        s = p;
+        c = __ffma2_rn(ch, XL, __ffma2_rn(cl, X, pe));
+    }
+    __device__ __forceinline__ void add(float4 A, float xh, float xl)
+    {
+        const float2 X = make_float2(xh, xh), XL = make_float2(xl, xl);
+        const float2 ch = make_float2(A.x, A.y), cl = make_float2(A.z, A.w);
+        const float2 p = __fmul2_rn(ch, X);
+        const float2 pe = __ffma2_rn(ch, X, pneg(p));
+        // TwoSum(s, p) lane by lane
+        const float2 t = __fadd2_rn(s, p);
+        const float2 bp = __fadd2_rn(t, pneg(s));
+        const float2 e = __fadd2_rn(__fadd2_rn(s, pneg(__fadd2_rn(t, pneg(bp)))), __fadd2_rn(p, pneg(bp)));
+        s = t;
+        c = __fadd2_rn(c, __fadd2_rn(e, __ffma2_rn(ch, XL, __ffma2_rn(cl, X, pe))));
+    }
+};
+
 // psi = sum_j sqrt(kappa_j) rho~_j at one node (Eq. 4)
 template <int NC>
 __device__ __forceinline__ F2 psi(const Params &P, const float (&h)[NC], const float (&l)[NC])
@@ -98,12 +129,20 @@ __device__ __forceinline__ void mu(const Params &P, const float4 *__restrict__ t
     // Eq. (10): T_i = rho~ sum_j x_j (a alpha)_ij, Q = rho~^2 (a alpha)_m
     F2 T[NC];
 #pragma unroll
-    for (int i = 0; i < NC; ++i) {
-        Dot t;
-        t.first(f2(P.dA[i * kMaxNc]), {h[0], l[0]});
+    for (int r = 0; r < NC / 2; ++r) {  // rows 2r, 2r+1 on the two lanes
+        Dot2x t;
+        t.first(P.dAp[r * kMaxNc], h[0], l[0]);
 #pragma unroll
-        for (int j = 1; j < NC; ++j) t.add(f2(P.dA[i * kMaxNc + j]), {h[j], l[j]});
-        T[i] = t.value();
+        for (int j = 1; j < NC; ++j) t.add(P.dAp[r * kMaxNc + j], h[j], l[j]);
+        T[2 * r] = fast_two_sum(t.s.x, t.c.x);
+        T[2 * r + 1] = fast_two_sum(t.s.y, t.c.y);
+    }
+    if constexpr (NC % 2 == 1) {
+        Dot t;
+        t.first(f2(P.dA[(NC - 1) * kMaxNc]), {h[0], l[0]});
+#pragma unroll
+        for (int j = 1; j < NC; ++j) t.add(f2(P.dA[(NC - 1) * kMaxNc + j]), {h[j], l[j]});
+        T[NC - 1] = t.value();
     }
     Dot qd;
     qd.first(y[0], T[0]);
