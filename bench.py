@@ -443,7 +443,7 @@ def fp64_one_at_a_time(lbmfug, d, jobs, order, tol, every, cap, budget_s):
         if time.perf_counter() - t0 > budget_s:
             break
         T, rho = jobs[k]
-        bar = max(tol, 8 * ulp32(1.05 * rho.max()))
+        bar = max(tol, 8 * ulp32(1.05 * rho.sum(axis=0).max()))
         p = lbmfug.Problem(0, rho.shape[2], rho.shape[1], 1, d["a"], d["b"], d["omega"], np.asarray(d["kij"]),
                            T, d["tau"], precision=lbmfug.LBM_FP64, kappa_ref=d["kappa_ref"])
         p.init_fields(rho[:, None])
@@ -482,10 +482,12 @@ def run_batched(args, lbmfug, local):
     rng = np.random.default_rng(5)
     sample = rng.permutation(len(jobs))
     errs = tie_line_errors(d, jobs, states, sample[:48])
-    s64, w64, ns64 = fp64_one_at_a_time(lbmfug, d, jobs, sample, tol, every, cap, args.batch_fp64_s)
+    # the binary64 path on slabs the batched form solved, in the same seeded order
+    solved = [k for k in sample if states[k]["converged"]]
+    s64, w64, ns64 = fp64_one_at_a_time(lbmfug, d, jobs, solved, tol, every, cap, args.batch_fp64_s)
     unconv = [k for k, s in enumerate(states) if not s["converged"] and not s["failed"]]
     return {"jobs": len(jobs), "converged": conv, "failed": failed,
-            "criterion": f"max|drho| per {every} steps < max({tol}, 8 ulp_binary32(largest density))",
+            "criterion": f"max|drho| per {every} steps < max({tol}, 8 ulp_binary32(largest total density))",
             "max_steps": cap, "wall_s": wall, "setup_s": t1 - t0, "solves_per_s": conv / wall,
             "node_steps_per_s": node_steps / wall, "threads": info["threads"], "ctas": info["ctas"],
             "rounds": info["rounds"], "precision": "fp32 (binary32 state and thermodynamics)",
@@ -495,7 +497,8 @@ def run_batched(args, lbmfug, local):
             "fp64_one_at_a_time": {"measured": True, "solves": s64, "wall_s": w64,
                                    "solves_per_s": s64 / w64 if w64 > 0 else None,
                                    "node_steps_per_s": ns64 / w64 if w64 > 0 else None,
-                                   "sample": "slabs of the sweep in a seeded random order, each to the criterion"}}
+                                   "sample": "slabs the batched form converged, in a seeded random order, "
+                                             "each alone to the same criterion"}}
 
 
 SERVE_FILE = os.path.join(ROOT, "paper_2306_10652_gb300", "workloads", "served_requests.json")
@@ -549,7 +552,7 @@ def run_served(args, lbmfug):
         if time.perf_counter() - b0 > args.serve_fp64_s:
             break
         r, rho = reqs[k], fields[k]
-        bar = max(tol, 8 * ulp32(1.05 * rho.max()))
+        bar = max(tol, 8 * ulp32(1.05 * rho.sum(axis=0).max()))
         prob = lbmfug.Problem(r["lattice"], r["nx"], r["ny"], r["nz"], r["a"], r["b"], r["omega"],
                               np.asarray(r["kij"]), r["T"], d["tau"], precision=lbmfug.LBM_FP64,
                               kappa_ref=d["kappa_ref"])
@@ -567,7 +570,7 @@ def run_served(args, lbmfug):
     return {"requests": len(reqs), "converged": len(conv),
             "exhausted": sum(p["state"] == "exhausted" for p in polls),
             "failed": sum(p["state"] == "failed" for p in polls),
-            "criterion": f"max|drho| per {every} steps < max({tol}, 8 ulp_binary32(1.05 x largest density)), "
+            "criterion": f"max|drho| per {every} steps < max({tol}, 8 ulp_binary32(1.05 x largest total density)), "
                          f"cap {cap} steps",
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
             "latency_over": "converged requests",
@@ -626,7 +629,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-jobs", type=int, default=None, help="first N jobs of the sweep")
-    ap.add_argument("--batch-max-steps", type=int, default=400000)
+    ap.add_argument("--batch-max-steps", type=int, default=1000000)
     ap.add_argument("--batch-fp64-s", type=float, default=60.0, help="seconds of the binary64 one-at-a-time sample")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--serve-slots", type=int, default=8)

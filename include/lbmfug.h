@@ -64,9 +64,18 @@ enum lbm_lattice { LBM_D2Q9 = 0, LBM_D3Q19 = 1 };
  *               keeps them in binary64). */
 enum lbm_precision { LBM_FP64 = 0, LBM_FP32DEV = 1, LBM_FP32 = 2 };
 
-/* Kernel schedule: LBM_SCHED_AUTO picks the fused single-pass kernel where it
- * exists (D2Q9) and the three-pass kernels otherwise. */
-enum lbm_schedule { LBM_SCHED_AUTO = 0, LBM_SCHED_THREEPASS = 1, LBM_SCHED_FUSED = 2 };
+/* Kernel schedule.
+ *  LBM_SCHED_FUSED:     D2Q9 only: one step kernel that walks rows with the
+ *                       densities, psi and mu rows on chip (LBM_FP32DEV adds
+ *                       a pass that forms the double-binary32 grad mu).
+ *  LBM_SCHED_MULTIPASS: LBM_FP32DEV on any lattice: a mu pass (double-
+ *                       binary32), a collision pass (binary32) and a density
+ *                       update that also forms psi for the next step.
+ *  LBM_SCHED_THREEPASS: any lattice and storage, thermodynamics and forces
+ *                       in binary64.
+ *  LBM_SCHED_AUTO:      fused on D2Q9; multi-pass for LBM_FP32DEV on D3Q19;
+ *                       three-pass otherwise. */
+enum lbm_schedule { LBM_SCHED_AUTO = 0, LBM_SCHED_THREEPASS = 1, LBM_SCHED_FUSED = 2, LBM_SCHED_MULTIPASS = 3 };
 
 enum lbm_status {
     LBM_OK = 0,
@@ -100,6 +109,16 @@ typedef struct lbm_options {
     lbm_alloc_fn alloc;   /* NULL = cudaMalloc */
     lbm_free_fn free;     /* must be set together with alloc */
     void *alloc_ctx;
+    int tune;             /* fused schedule: 1 (default) = the first lbm_step times
+                             candidate launch geometries (strips per row, segment
+                             waves, mu-pass waves) on the problem itself and keeps
+                             the fastest, cached for the process by (precision, Nc,
+                             nx, ny); 0 = the built-in geometry.  The geometry does
+                             not change any result (every node's arithmetic is the
+                             same); the first lbm_step then synchronises once. */
+    int strip;            /* > 0: interior columns per CTA of the fused kernel (forces
+                             the geometry, no tuning); 0 = automatic */
+    int seg_h;            /* > 0: rows per CTA of the fused kernel; 0 = automatic */
 } lbm_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -264,8 +283,8 @@ int lbm_batch_create(lbm_batch **out, int Nc, const double *a, const double *b, 
 /* Run rounds of check_every steps until every problem has finished or
  * max_steps steps have been taken.  A problem finishes when the largest
  * change of its densities over a round is below max(tol, 8 ulp) (converged),
- * ulp being the spacing of binary32 numbers at the problem's largest
- * density (the stored populations are binary32, and below that their
+ * ulp being the spacing of binary32 numbers at the problem's largest total
+ * density sum_i rho_i (the stored populations are binary32, and below that their
  * rounding, not relaxation, moves the densities), or when a density is not
  * finite (failed; it is retired and the others go on).  tol = 0 runs every
  * problem to max_steps.
@@ -297,7 +316,7 @@ int lbm_batch_destroy(lbm_batch *b);
  * stream, advanced in rounds of check_every steps whose kernels overlap on
  * the GPU; a job finishes when the largest density change over a round is
  * below tol (converged; with binary32 storage and tol > 0 below max(tol,
- * 8 ulp of binary32 at 1.05 times its largest initial density)), when a density is
+ * 8 ulp of binary32 at 1.05 times its largest initial total density)), when a density is
  * not finite (failed) or after
  * max_steps steps (exhausted), and its memory goes to the next request.
  * ------------------------------------------------------------------------ */

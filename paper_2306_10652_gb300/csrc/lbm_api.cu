@@ -4,10 +4,14 @@
 // paper (Sec. 2.3: a_i, b_i, omega_i, delta_ij, T; Sec. 2.1: tau; Sec. 2.2:
 // kappa_ref) into the per-problem constant block, manages device memory and
 // dispatches to the kernels.  No exception or abort crosses the ABI.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "lbm_df64.cuh"
@@ -31,6 +35,11 @@ struct lbm_problem {
     long long steps = 0;
     int sticky = LBM_OK;
     bool fused = false;
+    bool tuned = false;        // fused: the launch geometry is final
+    int nsm = 152;
+    bool multipass = false;
+    bool psi_valid = false;    // multi-pass: psi2 holds psi of the current state
+    float2 *psi2 = nullptr;    // multi-pass: psi [N] (hi, lo)
     FusedGeom geo{};
     StateBufs st[2];  // two time levels
     int cur = 0;
@@ -51,6 +60,11 @@ struct lbm_problem {
 };
 
 namespace {
+
+struct TuneCand {
+    int extra, seg, mseg;  // extra strips, segment waves, mu-pass waves
+};
+std::vector<TuneCand> tune_candidates(const lbm_problem *p);
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ECUDA; }
 
@@ -186,8 +200,11 @@ int ensure_allocated(lbm_problem *p)
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int sched = p->opt.schedule;
     const bool can_fuse = fused_supported(p->lattice, p->opt.precision, p->nc);
+    const bool can_mp = multipass_supported(p->lattice, p->opt.precision, p->nc, p->N);
     if (sched == LBM_SCHED_FUSED && !can_fuse) return LBM_ENOTSUP;
-    p->fused = can_fuse && sched != LBM_SCHED_THREEPASS;
+    if (sched == LBM_SCHED_MULTIPASS && !can_mp) return LBM_ENOTSUP;
+    p->fused = can_fuse && (sched == LBM_SCHED_FUSED || sched == LBM_SCHED_AUTO);
+    p->multipass = can_mp && (sched == LBM_SCHED_MULTIPASS || (sched == LBM_SCHED_AUTO && !p->fused));
     const bool f32 = p->opt.precision != LBM_FP64;
     const size_t nf = (size_t)p->nc * p->N;  // one field per component
     for (int k = 0; k < 2; ++k) {
@@ -224,17 +241,113 @@ int ensure_allocated(lbm_problem *p)
         !p->partials || !p->res || !p->flag)
         return LBM_ENOMEM;
     if (p->fused) {
-        p->geo = fused_geometry(p->opt.precision, p->nc, p->P, nsm);
-        p->mass_partials =
-            (double *)dev_alloc(p, (size_t)p->geo.nstrips * p->geo.segs * p->nc * sizeof(double));
+        p->nsm = nsm;
+        size_t parts = 0;
+        if (p->opt.strip > 0 || p->opt.seg_h > 0) {
+            p->geo = fused_geometry_forced(p->opt.precision, p->nc, p->P, nsm, p->opt.strip, p->opt.seg_h);
+            p->tuned = true;  // the caller chose the geometry
+            parts = (size_t)p->geo.nstrips * p->geo.segs;
+        } else {
+            p->geo = fused_geometry(p->opt.precision, p->nc, p->P, nsm);
+            p->tuned = !p->opt.tune;
+            for (const TuneCand &c : tune_candidates(p)) {  // room for every candidate's partials
+                const FusedGeom g = fused_geometry(p->opt.precision, p->nc, p->P, nsm, c.extra, c.seg, c.mseg);
+                parts = std::max(parts, (size_t)g.nstrips * g.segs);
+            }
+        }
+        p->mass_partials = (double *)dev_alloc(p, parts * p->nc * sizeof(double));
         if (!p->mass_partials || p->geo.nstrips < 1) return LBM_ENOMEM;
         if (p->opt.precision == LBM_FP32DEV) {
             p->mu = (float2 *)dev_alloc(p, nf * sizeof(float2));  // grad mu_i, written by the mu pass
             if (!p->mu || p->geo.mnstrips < 1) return LBM_ENOMEM;
         }
     }
+    if (p->multipass) {
+        p->mu = (float2 *)dev_alloc(p, nf * sizeof(float2));
+        p->psi2 = (float2 *)dev_alloc(p, (size_t)p->N * sizeof(float2));
+        if (!p->mu || !p->psi2) return LBM_ENOMEM;
+    }
     if (cudaMemsetAsync(p->flag, 0, 16, p->stream) != cudaSuccess) return LBM_ECUDA;
     p->allocated = true;
+    return LBM_OK;
+}
+
+// ---- launch-geometry tuner of the fused schedule -------------------------------
+std::vector<TuneCand> tune_candidates(const lbm_problem *p)
+{
+    std::vector<TuneCand> c;
+    const bool df = p->opt.precision == LBM_FP32DEV;
+    for (int extra = 0; extra <= 1; ++extra)
+        for (int seg = 1; seg <= 2; ++seg)
+            for (int mseg = 1; mseg <= (df ? 2 : 1); ++mseg) c.push_back({extra, seg, mseg});
+    return c;
+}
+
+struct TuneKey {
+    int prec, nc, nx, ny;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::tie(prec, nc, nx, ny) < std::tie(o.prec, o.nc, o.nx, o.ny);
+    }
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, TuneCand> g_tune_cache;
+
+// Time every candidate geometry on the problem's own state: each trial steps
+// st[cur] -> st[cur ^ 1] without swapping, so the state is untouched.
+int tune_geometry(lbm_problem *p)
+{
+    const TuneKey key{p->opt.precision, p->nc, p->nx, p->ny};
+    TuneCand best{0, 1, 1};
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            best = it->second;
+            cached = true;
+        }
+    }
+    if (!cached) {
+        cudaEvent_t e0, e1;
+        if (cudaEventCreate(&e0) != cudaSuccess) return LBM_ECUDA;
+        if (cudaEventCreate(&e1) != cudaSuccess) {
+            cudaEventDestroy(e0);
+            return LBM_ECUDA;
+        }
+        float best_ms = 1e30f;
+        int st = LBM_OK;
+        for (const TuneCand &c : tune_candidates(p)) {
+            const FusedGeom g = fused_geometry(p->opt.precision, p->nc, p->P, p->nsm, c.extra, c.seg, c.mseg);
+            int nl = 0, e = 0;
+            for (int k = 0; k < 4 && !e; ++k) {
+                if (k == 1) e = (int)cudaEventRecord(e0, p->stream);
+                if (!e)
+                    e = launch_fused_step(p->opt.precision, p->nc, p->P, g, p->st[p->cur], p->st[p->cur ^ 1],
+                                          nullptr, p->mu, &nl, p->stream);
+                p->launches += nl;
+            }
+            if (!e) e = (int)cudaEventRecord(e1, p->stream);
+            if (!e) e = (int)cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (!e) e = (int)cudaEventElapsedTime(&ms, e0, e1);
+            if (e) {
+                st = LBM_ECUDA;
+                break;
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (st) return st;
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune_cache[key] = best;
+    }
+    p->geo = fused_geometry(p->opt.precision, p->nc, p->P, p->nsm, best.extra, best.seg, best.mseg);
+    p->tuned = true;
     return LBM_OK;
 }
 
@@ -243,6 +356,7 @@ int finish_init(lbm_problem *p)
     p->cur = 0;
     p->steps = 0;
     p->have_snap = false;
+    p->psi_valid = false;
     p->monitor_step = -1;
     if (cudaMemsetAsync(p->flag, 0, 16, p->stream) != cudaSuccess) return LBM_ECUDA;
     if (p->fused && p->opt.precision == LBM_FP64) {
@@ -278,6 +392,7 @@ int lbm_options_default(lbm_options *opt)
     opt->kappa_ref_index = 0;
     opt->M = nullptr;
     opt->R = 1.0;
+    opt->tune = 1;
     return LBM_OK;
 }
 
@@ -333,11 +448,12 @@ int lbm_set_options(lbm_problem *p, const lbm_options *opt)
     if (p->allocated) return LBM_ESTATE;
     if (opt->precision != LBM_FP64 && opt->precision != LBM_FP32DEV && opt->precision != LBM_FP32)
         return LBM_EINVAL;
-    if (opt->schedule < LBM_SCHED_AUTO || opt->schedule > LBM_SCHED_FUSED) return LBM_EINVAL;
+    if (opt->schedule < LBM_SCHED_AUTO || opt->schedule > LBM_SCHED_MULTIPASS) return LBM_EINVAL;
     if (!(opt->kappa_ref >= 0.0) || !std::isfinite(opt->kappa_ref)) return LBM_EINVAL;
     if (opt->kappa_ref_index < 0 || opt->kappa_ref_index >= p->nc) return LBM_EINVAL;
     if (!(opt->R > 0.0) || !std::isfinite(opt->R)) return LBM_EINVAL;
     if ((opt->alloc == nullptr) != (opt->free == nullptr)) return LBM_EINVAL;
+    if (opt->strip < 0 || opt->seg_h < 0 || opt->tune < 0 || opt->tune > 1) return LBM_EINVAL;
     if (opt->M)
         for (int i = 0; i < p->nc; ++i)
             if (!(opt->M[i] > 0.0) || !std::isfinite(opt->M[i])) return LBM_EINVAL;
@@ -391,6 +507,13 @@ int lbm_step(lbm_problem *p, long long n)
     if (!p->initialized) return LBM_ESTATE;
     if (p->sticky) return p->sticky;
     const int every = p->opt.monitor_every;
+    if (n > 0 && p->fused && !p->tuned) {
+        const int st = tune_geometry(p);
+        if (st) {
+            p->sticky = st;
+            return st;
+        }
+    }
     for (long long s = 0; s < n; ++s) {
         const bool mon = every > 0 && ((p->steps + 1) % every == 0);
         int e;
@@ -404,6 +527,16 @@ int lbm_step(lbm_problem *p, long long n)
                 e = launch_fused_mass_final(p->nc, p->geo, p->mass_partials, p->mon, p->flag, p->stream);
                 p->launches += 1;
             }
+        } else if (p->multipass) {
+            if (!p->psi_valid) {
+                e = launch_multipass_psi(p->lattice, p->nc, p->P, p->st[p->cur], p->psi2, p->stream);
+                p->launches += 1;
+                p->psi_valid = true;
+            }
+            if (!e)
+                e = launch_multipass_step(p->lattice, p->nc, p->P, p->st[p->cur], p->st[p->cur ^ 1], p->psi2,
+                                          p->mu, p->w.osum, p->w.ocmp, p->stream);
+            p->launches += 3;
         } else {
             e = launch_threepass_step(p->lattice, sprec(p), p->nc, p->P, p->st[p->cur],
                                       p->st[p->cur ^ 1], p->w, p->stream);
@@ -416,6 +549,7 @@ int lbm_step(lbm_problem *p, long long n)
         p->cur ^= 1;
         p->steps++;
         if (mon && !p->fused) {
+            // (the multi-pass schedule's psi of the new state stays valid: moments do not touch it)
             // mass of the new state: densities by the first pass of the next step's kernels
             e = launch_fields(p->lattice, sprec(p), p->nc, p->P, p->st[p->cur], p->w, p->w.rho,
                               nullptr, nullptr, nullptr, p->stream);

@@ -255,7 +255,12 @@ __global__ void k_batch_round(const Shared S, const Job *__restrict__ jobs, Stat
             const float d = (float)fabs(now - was);
             finite = finite && isfinite(now);
             dmax = fmaxf(dmax, d);
-            rmax = fmaxf(rmax, RH[k]);
+        }
+        for (int n = t; n < N; n += T) {  // largest total density of the job
+            float tot = 0.0f;
+#pragma unroll
+            for (int i = 0; i < NC; ++i) tot += RH[i * N + n];
+            rmax = fmaxf(rmax, tot);
         }
         if (!finite) dmax = INFINITY;
 #pragma unroll
@@ -279,7 +284,7 @@ __global__ void k_batch_round(const Shared S, const Job *__restrict__ jobs, Stat
                 r = fmaxf(r, s_rmax[w]);
             }
             // the stored populations are binary32: below 8 ulp of the largest
-            // density a change is their rounding jitter, not relaxation
+            // total density a change is their rounding jitter, not relaxation
             const double bar = tol > 0.0 ? fmax(tol, 8.0 * ulp32(r)) : 0.0;  // tol = 0: run to the step cap
             Status &st = status[jid];
             st.cur = cur;

@@ -67,18 +67,24 @@ bool fused_supported(int lat, int prec, int nc)
     return o && o->smem(o->wmax) <= max_optin_smem();
 }
 
-FusedGeom fused_geometry(int prec, int nc, const Params &P, int num_sms)
+// Launch geometry: strips of at most wmax columns (extra_strips more than the
+// fewest, balanced), segments filling seg_mult waves of the resident CTA
+// slots; the mu pass of LBM_FP32DEV likewise with mseg_mult waves.
+FusedGeom fused_geometry(int prec, int nc, const Params &P, int num_sms, int extra_strips, int seg_mult,
+                         int mseg_mult)
 {
     FusedGeom g{};
     const fz::Ops *o = lookup(prec, nc);
     if (!o) return g;
     g.threads = fz::kT;
-    g.nstrips = (P.nx + o->wmax - 1) / o->wmax;
+    g.nstrips = (P.nx + o->wmax - 1) / o->wmax + (extra_strips > 0 ? extra_strips : 0);
+    if (g.nstrips > P.nx) g.nstrips = P.nx;
     g.strip = (P.nx + g.nstrips - 1) / g.nstrips;   // balanced strip width <= wmax
+    g.nstrips = (P.nx + g.strip - 1) / g.strip;
     g.smem = o->smem(g.strip);
     int per_sm = o->occupancy(g.smem);
     if (per_sm < 1) per_sm = 1;
-    const long long slots = (long long)num_sms * per_sm;
+    const long long slots = (long long)num_sms * per_sm * (seg_mult > 0 ? seg_mult : 1);
     long long segs = slots / g.nstrips;
     if (segs < 1) segs = 1;
     if (segs > P.ny) segs = P.ny;
@@ -86,14 +92,33 @@ FusedGeom fused_geometry(int prec, int nc, const Params &P, int num_sms)
     g.segs = (P.ny + g.seg_h - 1) / g.seg_h;
     const int mper_sm = o->occupancy_mu();
     if (mper_sm > 0) {
-        // mu pass: strips of at most kT - 2 columns, segments filling every slot
+        // mu pass: strips of at most kT - 4 columns, segments filling the slots
         g.mnstrips = (P.nx + fz::kWmaxMu - 1) / fz::kWmaxMu;
         g.mstrip = (P.nx + g.mnstrips - 1) / g.mnstrips;
-        long long ms = (long long)num_sms * mper_sm / g.mnstrips;
+        long long ms = (long long)num_sms * mper_sm * (mseg_mult > 0 ? mseg_mult : 1) / g.mnstrips;
         if (ms < 1) ms = 1;
         if (ms > P.ny) ms = P.ny;
         g.mseg_h = (int)((P.ny + ms - 1) / ms);
         g.msegs = (P.ny + g.mseg_h - 1) / g.mseg_h;
+    }
+    return g;
+}
+
+// Caller-chosen strip width and segment height (0 = as fused_geometry).
+FusedGeom fused_geometry_forced(int prec, int nc, const Params &P, int num_sms, int strip, int seg_h)
+{
+    FusedGeom g = fused_geometry(prec, nc, P, num_sms, 0, 1, 1);
+    const fz::Ops *o = lookup(prec, nc);
+    if (!o || g.nstrips < 1) return g;
+    if (strip > 0) {
+        g.strip = strip < o->wmax ? strip : o->wmax;
+        if (g.strip > P.nx) g.strip = P.nx;
+        g.nstrips = (P.nx + g.strip - 1) / g.strip;
+        g.smem = o->smem(g.strip);
+    }
+    if (seg_h > 0) {
+        g.seg_h = seg_h < P.ny ? seg_h : P.ny;
+        g.segs = (P.ny + g.seg_h - 1) / g.seg_h;
     }
     return g;
 }

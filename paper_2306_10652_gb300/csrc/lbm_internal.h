@@ -66,7 +66,9 @@ int launch_state_from_f64(int lat, int prec, int nc, const Params &P, const doub
 // Fused D2Q9 schedule (lbm_fused2d.cu).  prec as the options: 0 binary64,
 // 1 binary32 storage with binary64 thermodynamics, 2 binary32 throughout.
 bool fused_supported(int lat, int prec, int nc);
-FusedGeom fused_geometry(int prec, int nc, const Params &P, int num_sms);
+FusedGeom fused_geometry(int prec, int nc, const Params &P, int num_sms, int extra_strips = 0,
+                         int seg_mult = 1, int mseg_mult = 1);
+FusedGeom fused_geometry_forced(int prec, int nc, const Params &P, int num_sms, int strip, int seg_h);
 // binary64 only: densities of the fused state from the populations
 int launch_fused_density(int prec, int nc, const Params &P, StateBufs st, cudaStream_t s);
 // mu: [nc][N] (hi, lo) chemical potentials of LBM_FP32DEV (else unused);
@@ -76,6 +78,14 @@ int launch_fused_step(int prec, int nc, const Params &P, const FusedGeom &geo, S
 // Sum the per-CTA mass partials of a monitored fused step into out[nc].
 int launch_fused_mass_final(int nc, const FusedGeom &geo, const double *partials, double *out,
                             int *nonfinite, cudaStream_t s);
+
+// Binary32 multi-pass schedule of LBM_FP32DEV on any lattice
+// (lbm_multipass.cu): psi [N] (hi, lo) of the current state, mu [nc][N]
+// (hi, lo) scratch, osum/ocmp [nc][N] departures.
+bool multipass_supported(int lat, int prec, int nc, long long N);
+int launch_multipass_psi(int lat, int nc, const Params &P, StateBufs st, float2 *psi, cudaStream_t s);
+int launch_multipass_step(int lat, int nc, const Params &P, StateBufs in, StateBufs out, float2 *psi,
+                          float2 *mu, float *osum, float *ocmp, cudaStream_t s);
 
 // Chemical potentials and forces of a D2Q9 state from its binary64 densities
 // (lbm_fields_*.cu).  prec: 0 binary64, 1 double-binary32, 2 binary32

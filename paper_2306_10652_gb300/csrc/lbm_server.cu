@@ -125,8 +125,13 @@ struct lbm_server {
         // below 8 ulp of binary32 at the largest density count as converged
         r->bar = r->tol;
         if (r->precision != LBM_FP64 && r->tol > 0.0) {
-            double rmax = 0.0;
-            for (double v : r->rho) rmax = std::max(rmax, v);
+            double rmax = 0.0;  // largest total density over the nodes
+            const size_t nn = r->rho.size() / (size_t)r->nc;
+            for (size_t k = 0; k < nn; ++k) {
+                double tot = 0.0;
+                for (int i = 0; i < r->nc; ++i) tot += r->rho[(size_t)i * nn + k];
+                rmax = std::max(rmax, tot);
+            }
             int e = 0;
             std::frexp(1.05 * rmax, &e);  // 1.05 rmax in [2^(e-1), 2^e)
             r->bar = std::max(r->tol, 8.0 * std::ldexp(1.0, e - 1 - 23));

@@ -24,7 +24,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 LBM_D2Q9, LBM_D3Q19 = 0, 1
 LBM_FP64, LBM_FP32DEV, LBM_FP32 = 0, 1, 2
-LBM_SCHED_AUTO, LBM_SCHED_THREEPASS, LBM_SCHED_FUSED = 0, 1, 2
+LBM_SCHED_AUTO, LBM_SCHED_THREEPASS, LBM_SCHED_FUSED, LBM_SCHED_MULTIPASS = 0, 1, 2, 3
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENONFINITE, LBM_ETIMEOUT, LBM_ESTATE, LBM_ENOTSUP = \
     0, -1, -2, -3, -4, -5, -6, -7
 LBM_MAX_NC = 16
@@ -40,7 +40,8 @@ class lbm_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("schedule", ctypes.c_int),
                 ("kappa_ref", ctypes.c_double), ("kappa_ref_index", ctypes.c_int),
                 ("M", _dp), ("R", ctypes.c_double), ("stream", _vp), ("monitor_every", ctypes.c_int),
-                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", _vp)]
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", _vp),
+                ("tune", ctypes.c_int), ("strip", ctypes.c_int), ("seg_h", ctypes.c_int)]
 
 
 def _sig(name, res, *args):
@@ -180,7 +181,7 @@ class Problem:
 
     def __init__(self, lattice, nx, ny, nz, a, b, omega, kij=None, T=None, tau=1.0, *,
                  precision=LBM_FP64, schedule=LBM_SCHED_AUTO, kappa_ref=0.02, kappa_ref_index=0,
-                 M=None, R=1.0, stream=None, monitor_every=0):
+                 M=None, R=1.0, stream=None, monitor_every=0, tune=1, strip=0, seg_h=0):
         self._h = None
         a = _host(a)
         nc = a.size
@@ -206,6 +207,9 @@ class Problem:
         opt.R = float(R)
         opt.stream = None if stream is None else ctypes.c_void_p(int(stream))
         opt.monitor_every = int(monitor_every)
+        opt.tune = int(tune)
+        opt.strip = int(strip)
+        opt.seg_h = int(seg_h)
         _check(_lib.lbm_set_options(self._h, ctypes.byref(opt)), "lbm_set_options")
 
     # -- shapes --

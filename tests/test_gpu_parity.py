@@ -35,7 +35,7 @@ from paper_2306_10652_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 FP64, FP32DEV, FP32 = 0, 1, 2
-THREEPASS, AUTO, FUSED = 1, 0, 2
+THREEPASS, AUTO, FUSED, MULTIPASS = 1, 0, 2, 3
 
 
 def lb():
@@ -83,8 +83,8 @@ def test_one_step_fp64(case, schedule):
     assert one_step_case(seed, nc, lattice, shape, tau, Mr, FP64, schedule) < 1e-12
 
 
-@pytest.mark.parametrize("case", CASES[:6] + CASES[8:10], ids=lambda c: f"lat{c[2]}-nc{c[1]}")
-@pytest.mark.parametrize("schedule", [THREEPASS, AUTO])
+@pytest.mark.parametrize("case", CASES[:6] + CASES[8:11], ids=lambda c: f"lat{c[2]}-nc{c[1]}")
+@pytest.mark.parametrize("schedule", [THREEPASS, AUTO, MULTIPASS])
 def test_one_step_fp32dev(case, schedule):
     seed, nc, lattice, shape, tau, Mr = case
     assert one_step_case(seed, nc, lattice, shape, tau, Mr, FP32DEV, schedule) < 2e-6
@@ -198,7 +198,7 @@ def test_moments_match_oracle(lattice, shape, nc):
 
 
 @pytest.mark.parametrize("precision,schedule", [(FP64, THREEPASS), (FP64, AUTO), (FP32DEV, AUTO),
-                                                (FP32, AUTO)])
+                                                (FP32, AUTO), (FP32DEV, MULTIPASS)])
 def test_mass_conservation_and_uniform_fixed_point(precision, schedule):
     shape = (1, 40, 70)
     c = seeded_mixture(31, 3, 0, shape)
@@ -294,3 +294,50 @@ def test_fused_matches_threepass_many_shapes():
                 out.append(gp.get_state())
         scale = np.abs(out[0]).max()
         assert np.abs(out[0] - out[1]).max() <= 1e-12 * scale, shape
+
+
+@pytest.mark.parametrize("lattice,shape,nc,steps", [(1, (6, 7, 9), 3, 5), (1, (5, 4, 6), 10, 3), (0, (1, 33, 70), 4, 5)])
+def test_multipass_several_steps(lattice, shape, nc, steps):
+    """The multi-pass schedule (density update and psi of the next step in one
+    pass) against the oracle over several steps: within 2e-6 of max |g_i|
+    per step (a few binary32 roundings per step on each population)."""
+    err = one_step_case(300 + nc, nc, lattice, shape, precision=FP32DEV, schedule=MULTIPASS, nsteps=steps)
+    assert err < 2e-6 * steps, err
+
+
+def test_multipass_is_the_d3q19_default_for_fp32dev():
+    """AUTO runs LBM_FP32DEV on D3Q19 with the multi-pass schedule: three
+    launches per step (plus one psi pass after initialisation)."""
+    shape = (6, 5, 4)
+    c = seeded_mixture(310, 3, 1, shape)
+    rho = smooth_rho(310, c, shape)
+    with gpu_problem(c, 1, shape, precision=FP32DEV) as gp:
+        gp.init_fields(rho)
+        l0 = gp.launch_count()
+        gp.step(4)
+        assert gp.launch_count() - l0 == 1 + 3 * 4
+        assert gp.schedule_info()["fused"] == 0
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32DEV, FP32], ids=["fp64", "fp32dev", "fp32"])
+def test_launch_geometry_changes_no_result(precision):
+    """The fused kernels' result does not depend on the launch geometry (each
+    node's arithmetic and the order of its density sums are the same in every
+    strip and segment): forced strip widths and segment heights, the tuned
+    geometry and the built-in one give bitwise equal states."""
+    shape = (1, 45, 200)
+    c = seeded_mixture(320, 4, 0, shape)
+    rho = smooth_rho(320, c, shape)
+    u = synth.random_velocity(320, 2, shape, 1e-3)
+    out = []
+    for kw in (dict(tune=0), dict(tune=1), dict(strip=37, seg_h=5), dict(strip=100, seg_h=45),
+               dict(strip=7, seg_h=1)):
+        with gpu_problem(c, 0, shape, precision=precision, schedule=FUSED, **kw) as gp:
+            gp.init_fields(rho, u)
+            gp.step(6)
+            out.append(gp.get_state())
+            info = gp.schedule_info()
+            if "strip" in kw:
+                assert (info["strip"], info["seg_h"]) == (kw["strip"], kw["seg_h"]), info
+    for o in out[1:]:
+        assert np.array_equal(o, out[0])
