@@ -49,17 +49,21 @@ def initial_density(d, case, nx, ny, seed=2):
     return (rho * synth.multiplicative_noise(seed, rho.shape, 0.01))[:, None]  # [nc, 1, ny, nx]
 
 
-# DRAM bytes per node-step of the fused binary32 step at Nc = 10, from the ncu
-# capture summarised in profiles/fused32_fp32_spinodal2048_nc10.md (2048 x 512
-# case: dram read + write = 836.6 MB over 1,048,576 nodes).  The traffic is
-# per node (strip/segment halos come from L2), so it scales with the nodes of
-# a launch.  None for any other form or Nc, or once the kernel changes.
-NCU_TRAFFIC_B_PER_NODE = {}
+# DRAM bytes per node of one launch of the dominant kernel (ncu dram__bytes_read
+# + dram__bytes_write on a 2048 x 1024 case, larger than L2), keyed on (form,
+# schedule, Nc) and on the kernel they were captured from; the traffic is per
+# node (strip and segment halos come from L2), so it scales with the nodes of a
+# launch.  profiles/fp32dev_mu_pass_and_step_spinodal2048_nc10.md: the step
+# kernel k_fused32<10, DF64> moved 1062.2 + 799.0 MB over 2,097,152 nodes.
+# A form without an entry, or whose kernel has changed since, reports null.
+NCU_TRAFFIC_B_PER_NODE = {
+    ("fp32dev", "auto", 10): ("k_fused32<10, DF64> (step kernel)", (1062.237440e6 + 798.856960e6) / 2097152),
+}
 
 
 def traffic_per_launch(args, nc, N):
     v = NCU_TRAFFIC_B_PER_NODE.get((args.precision, args.schedule, nc))
-    return None if v is None else v * N
+    return (None, None) if v is None else (v[1] * N, v[0])
 
 
 def peaks():
@@ -217,7 +221,13 @@ def run_gpu(args):
             if pr == prec and sc == sched:
                 continue
             forms[name] = time_form(lbmfug, case, rho, nx, ny, pr, sc, k, 2, local)
+        # D3Q19 (no single-pass kernel): the multi-pass LBM_FP32DEV schedule and binary64
+        forms["d3q19_fp32dev_multipass"] = time_form_3d(lbmfug, case, 128, lbmfug.LBM_FP32DEV,
+                                                        lbmfug.LBM_SCHED_AUTO, 10, 3, local)
+        forms["d3q19_fp64_threepass"] = time_form_3d(lbmfug, case, 128, lbmfug.LBM_FP64,
+                                                     lbmfug.LBM_SCHED_AUTO, 2, 1, local)
     clocks = clk.summary()
+    traffic = traffic_per_launch(args, nc, N)
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
@@ -229,9 +239,12 @@ def run_gpu(args):
                    "parallelism": f"replicas{ws}" if ws > 1 else "single",
                    "l2": "inputs larger than L2 (populations %.2f GB per buffer)" % (9 * nc * spop * N / 1e9)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / pk["hbm_gbs"], "traffic": traffic_per_launch(args, nc, N),
+                     "frac": achieved / pk["hbm_gbs"], "traffic": traffic[0],
+                     "traffic_kernel": traffic[1],
                      "peak_kind": pk_kind, "algorithmic_bytes_per_node_step": 2 * 9 * nc * spop,
-                     "kernel": "fused step (k_fused32 / k_fused), one launch per step"},
+                     "kernel": ("step: mu pass k_mu32 + step kernel k_fused32 (LBM_FP32DEV), algorithmic "
+                                "bytes of the step over the step time" if prec == lbmfug.LBM_FP32DEV else
+                                "fused step kernel, one launch per step")},
         "forms": forms,
         "batched": batched,
         "served": served,
@@ -266,6 +279,40 @@ def time_form(lbmfug, case, rho, nx, ny, prec, sched, steps, warmup, local):
     prob.close()
     ms = e0.elapsed_time(e1)
     return {"value": case["nc"] * nx * ny * steps / (ms * 1e-3) / 1e9, "ms_per_step": ms / steps}
+
+
+def time_form_3d(lbmfug, case, n, prec, sched, steps, warmup, local):
+    """Nc-GLUPS and HBM fraction of one form on a D3Q19 n^3 box of the same
+    mixture (uniform composition, +-1 % seeded noise), CUDA events."""
+    import torch
+    from paper_2306_10652_gb300 import synth
+    nc = case["nc"]
+    z = np.asarray(case["z"])
+    rho = (z[:, None, None, None] * case["rho_molar_total"]) * synth.multiplicative_noise(12, (nc, n, n, n), 0.01)
+    stream = torch.cuda.Stream()
+    prob = lbmfug.Problem(1, n, n, n, case["a"], case["b"], case["omega"], np.asarray(case["kij"]),
+                          case["T"], case["tau"], precision=prec, schedule=sched, kappa_ref=case["kappa_ref"],
+                          stream=stream.cuda_stream)
+    d_rho = torch.from_numpy(rho.reshape(-1)).to(f"cuda:{local}")
+    prob.init_fields_device(d_rho)
+    del d_rho
+    prob.step(warmup)
+    prob.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    prob.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    prob.close()
+    ms = e0.elapsed_time(e1) / steps
+    N = n ** 3
+    spop = 8 if prec == lbmfug.LBM_FP64 else 4
+    alg = 2 * 19 * nc * spop * N
+    pk, _ = peaks()
+    return {"value": nc * N / (ms * 1e-3) / 1e9, "ms_per_step": ms, "box": f"D3Q19 {n}^3",
+            "roofline_frac": alg / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+            "algorithmic_bytes_per_node_step": 2 * 19 * nc * spop}
 
 
 def run_e2e(args, lbmfug, case, rho, nx, ny, prec, sched, local):

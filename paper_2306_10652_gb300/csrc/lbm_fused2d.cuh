@@ -378,7 +378,9 @@ constexpr int kWmaxMu = kT - 4;
 template <int NC> struct SmemMu {
     static __host__ __device__ constexpr size_t bytes()
     {
-        return (size_t)df::kLogTab * sizeof(float4) + 4 * kT * sizeof(float2) + 3 * NC * kT * sizeof(float2);
+        // log table, psi ring, mu ring, per-thread scratch of mu_rolled (PH, PL, TS)
+        return (size_t)df::kLogTab * sizeof(float4) + 4 * kT * sizeof(float2) + 3 * NC * kT * sizeof(float2) +
+               (size_t)NC * kT * (2 * sizeof(float) + sizeof(float2));
     }
 };
 
@@ -390,6 +392,9 @@ __global__ void __launch_bounds__(kT) k_mu32(const Params P, const int W, const 
     float4 *LT = (float4 *)smem;                                           // [128]
     float2 *PS = (float2 *)(smem + df::kLogTab * sizeof(float4));          // [4][kT]
     float2 *MU = PS + 4 * kT;                                              // [3][NC][kT]
+    float2 *TS = MU + 3 * NC * kT;                                         // [NC][kT] T_i
+    float *PHs = (float *)(TS + NC * kT);                                  // [NC][kT] pair hi
+    float *PLs = PHs + NC * kT;                                            // [NC][kT] pair lo
     const int nx = P.nx, ny = P.ny;
     const IDX N = (IDX)P.N;
     const int x0 = blockIdx.x * W;
@@ -427,10 +432,8 @@ __global__ void __launch_bounds__(kT) k_mu32(const Params P, const int W, const 
             const df::F2 lap = df::lap9(df::f2(p1[t]), df::f2(p1[t + 1]), df::f2(p1[t - 1]), df::f2(p2[t]),
                                         df::f2(p0[t]), df::f2(p2[t + 1]), df::f2(p2[t - 1]), df::f2(p0[t + 1]),
                                         df::f2(p0[t - 1]));
-            df::F2 m[NC];
-            df::mu<NC>(P, LT, ph, pl, lap, m);
-#pragma unroll
-            for (int i = 0; i < NC; ++i) MU[(((kk - 1) % 3) * NC + i) * kT + t] = make_float2(m[i].hi, m[i].lo);
+            df::mu_rolled<NC>(P, LT, ph, pl, lap, PHs + t, PLs + t, TS + t, kT,
+                              MU + ((kk - 1) % 3) * NC * kT + t, kT);
         }
         if (hasP) {
 #pragma unroll

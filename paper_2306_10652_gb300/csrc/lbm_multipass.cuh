@@ -83,16 +83,24 @@ __global__ void __launch_bounds__(kThreads) k_mp_psi(const Params P, StateBufs s
     }
 }
 
+// per-thread scratch of mu_rolled: PH, PL [NC] floats and TS [NC] float2
+template <int NC> constexpr size_t mp_mu_smem() { return (size_t)NC * kThreads * (2 * sizeof(float) + sizeof(float2)); }
+
 template <int LAT, int NC>
 __global__ void __launch_bounds__(kThreads)
     k_mp_mu(const Params P, StateBufs st, const float2 *__restrict__ psi, float2 *__restrict__ mu)
 {
     using L = Lattice<LAT>;
     __shared__ float4 LT[df::kLogTab];
-    for (int j = threadIdx.x; j < df::kLogTab; j += blockDim.x) LT[j] = P.logtab[j];
+    extern __shared__ __align__(16) unsigned char scratch[];
+    float2 *TS = (float2 *)scratch;
+    float *PH = (float *)(TS + NC * kThreads);
+    float *PL = PH + NC * kThreads;
+    const int t = threadIdx.x;
+    for (int j = t; j < df::kLogTab; j += blockDim.x) LT[j] = P.logtab[j];
     __syncthreads();
     const int N = (int)P.N;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < N; r += gridDim.x * blockDim.x) {
+    for (int r = blockIdx.x * blockDim.x + t; r < N; r += gridDim.x * blockDim.x) {
         int nb[L::Q];
         neighbours<LAT>(P, r, nb);
         float h[NC], l[NC];
@@ -101,10 +109,7 @@ __global__ void __launch_bounds__(kThreads)
             h[i] = __ldg(st.rhi_f() + (long long)i * N + r);
             l[i] = __ldg(st.rlo + (long long)i * N + r);
         }
-        df::F2 m[NC];
-        df::mu<NC>(P, LT, h, l, lapQ<LAT>(psi, nb), m);
-#pragma unroll
-        for (int i = 0; i < NC; ++i) mu[(long long)i * N + r] = make_float2(m[i].hi, m[i].lo);
+        df::mu_rolled<NC>(P, LT, h, l, lapQ<LAT>(psi, nb), PH + t, PL + t, TS + t, kThreads, mu + r, N);
     }
 }
 
@@ -275,7 +280,11 @@ template <int LAT, int NC> struct Impl {
                     float *ocmp, cudaStream_t s)
     {
         const unsigned G = grid_for(P.N);
-        k_mp_mu<LAT, NC><<<G, kThreads, 0, s>>>(P, in, ps, mu);
+        const size_t sm = mp_mu_smem<NC>();
+        if (sm > 48 * 1024 &&
+            cudaFuncSetAttribute(k_mp_mu<LAT, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+            return (int)cudaGetLastError();
+        k_mp_mu<LAT, NC><<<G, kThreads, sm, s>>>(P, in, ps, mu);
         k_mp_collide<LAT, NC><<<G, kThreads, 0, s>>>(P, in, out, mu, osum, ocmp);
         k_mp_update<LAT, NC><<<G, kThreads, 0, s>>>(P, in, out, osum, ocmp, ps);
         return (int)cudaGetLastError();

@@ -179,5 +179,91 @@ __device__ __forceinline__ void mu(const Params &P, const float4 *__restrict__ t
     }
 }
 
+// mu of one node with rolled loops over the row pairs of T_i and over the
+// components (the unrolled form above is a few thousand instructions of
+// straight-line code at Nc = 10, more than the instruction cache holds).
+// The same operations in the same order, so the result is bitwise that of
+// mu().  Per-thread scratch in shared memory with stride `pitch` floats:
+// PH, PL [NC] (the density pair), TS [NC] float2 (T_i); mu_i is written to
+// out[i * ostride].
+template <int NC>
+__device__ __forceinline__ void mu_rolled(const Params &P, const float4 *__restrict__ tab, const float (&h)[NC],
+                                          const float (&l)[NC], F2 lap, float *PH, float *PL, float2 *TS, int pitch,
+                                          float2 *out, int ostride)
+{
+    constexpr double kS2 = 1.41421356237309504880168872421;
+    F2 y[NC];
+    Dot rt;
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+        PH[i * pitch] = h[i];
+        PL[i * pitch] = l[i];
+        y[i] = Dot::term(f2(P.dM[i]), {h[i], l[i]});
+        if (i == 0) {
+            rt.s = y[0].hi;
+            rt.c = y[0].lo;
+        } else {
+            rt.add_term(y[i]);
+        }
+    }
+    const F2 rho = rt.value();
+    Dot bd;
+    bd.first(f2(P.dB[0]), {h[0], l[0]});
+#pragma unroll
+    for (int j = 1; j < NC; ++j) bd.add(f2(P.dB[j]), {h[j], l[j]});
+    const F2 B = bd.value();
+#pragma unroll 1
+    for (int r = 0; r < NC / 2; ++r) {
+        Dot2x t;
+        t.first(P.dAp[r * kMaxNc], h[0], l[0]);
+#pragma unroll
+        for (int j = 1; j < NC; ++j) t.add(P.dAp[r * kMaxNc + j], h[j], l[j]);
+        const F2 a = fast_two_sum(t.s.x, t.c.x), b = fast_two_sum(t.s.y, t.c.y);
+        TS[(2 * r) * pitch] = make_float2(a.hi, a.lo);
+        TS[(2 * r + 1) * pitch] = make_float2(b.hi, b.lo);
+    }
+    if constexpr (NC % 2 == 1) {
+        Dot t;
+        t.first(f2(P.dA[(NC - 1) * kMaxNc]), {h[0], l[0]});
+#pragma unroll
+        for (int j = 1; j < NC; ++j) t.add(f2(P.dA[(NC - 1) * kMaxNc + j]), {h[j], l[j]});
+        const F2 v = t.value();
+        TS[(NC - 1) * pitch] = make_float2(v.hi, v.lo);
+    }
+    Dot qd;
+    qd.first(y[0], f2(TS[0]));
+#pragma unroll
+    for (int i = 1; i < NC; ++i) qd.add(y[i], f2(TS[i * pitch]));
+    const F2 Q = qd.value();
+    const F2 one = {1.0f, 0.0f};
+    const F2 omB = add(one, neg(B));
+    const F2 den = add(one, mul(B, add({2.0f, 0.0f}, neg(B))));  // 1 + 2B - B^2
+    const F2 N1 = add(one, mul(B, {hi_of(1.0 + kS2), lo_of(1.0 + kS2)}));
+    const F2 N2 = add(one, mul(B, {hi_of(1.0 - kS2), lo_of(1.0 - kS2)}));
+    const F2 Lr = norm(log(div(N1, N2), tab));
+    const F2 lnomB = norm(log(omB, tab));
+    const F2 u = div(one, B), v = div(one, omB), w = div(one, den);
+    const F2 RT = f2(P.dRT);
+    const F2 Lu = mul(Lr, u);
+    const F2 RC1 = add(mul(mul(RT, rho), v),
+                       mul(mul(Q, u), add(mul(Lu, {hi_of(0.5 / kS2), lo_of(0.5 / kS2)}), neg(w))));
+    const F2 RC2 = mul(Lu, {hi_of(-1.0 / kS2), lo_of(-1.0 / kS2)});
+    const F2 RG = mul(RT, lnomB);
+#pragma unroll 1
+    for (int i = 0; i < NC; ++i) {
+        Dot a;
+        const F2 t0 = mul_u(RT, log({PH[i * pitch], PL[i * pitch]}, tab));
+        a.s = t0.hi;
+        a.c = t0.lo;
+        a.add_term(f2(P.dRK[i]));
+        a.add_term(neg(RG));
+        a.add_term(mul_u(f2(P.db[i]), RC1));
+        a.add_term(mul_u(f2(TS[i * pitch]), RC2));
+        a.add_term(neg(mul_u(f2(P.dsqk[i]), lap)));
+        const F2 m = a.value();
+        out[(long long)i * ostride] = make_float2(m.hi, m.lo);
+    }
+}
+
 }  // namespace df
 }  // namespace lbmfug
