@@ -127,6 +127,47 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+class BusySampler:
+    """nvidia-smi utilization.gpu (percent of time a kernel ran) every 200 ms."""
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", "--query-gpu=utilization.gpu",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.out.close()
+
+    def mean(self):
+        if self.proc is None:
+            return None
+        vals = []
+        for line in open(self.path):
+            try:
+                vals.append(float(line.strip()))
+            except ValueError:
+                pass
+        os.unlink(self.path)
+        return statistics.mean(vals) if vals else None
+
+
 def aggregate_replicas(ms, units, world_size, device="cpu"):
     """Replicas: the job time is the slowest rank's, the work is every rank's.
     Returns (max ms over ranks, sum of units over ranks); one process = as is."""
@@ -576,11 +617,11 @@ def run_served(args, lbmfug):
     reqs = d["requests"]
     tol, every, cap = 2e-6, 1000, args.serve_max_steps
     fields = [served_field(r, d["W"]) for r in reqs]
-    with lbmfug.Server(0.8, max_active=args.serve_slots) as srv:
+    with lbmfug.Server(0.8, max_active=args.serve_slots) as srv, BusySampler(0) as busy:
         t0 = time.perf_counter()
         ids = []
         for r, rho in zip(reqs, fields):
-            time.sleep(r["arrival_gap_s"])
+            time.sleep(r["arrival_gap_s"] / args.serve_rate)
             ids.append(srv.submit(r["lattice"], r["a"], r["b"], r["omega"], np.asarray(r["kij"]), r["T"], d["tau"],
                                   rho, precision=lbmfug.LBM_FP32DEV, check_every=every, max_steps=cap, tol=tol,
                                   kappa_ref=d["kappa_ref"]))
@@ -588,6 +629,7 @@ def run_served(args, lbmfug):
         t1 = time.perf_counter()
         polls = [srv.poll(j) for j in ids]
         stats = srv.stats()
+    busy_pct = busy.mean()
     conv = [p for p in polls if p["state"] == "converged"]
     lat = np.array([p["latency_s"] for p in conv]) if conv else np.array([np.nan])
     work = sum(p["steps"] * r["nc"] * r["nx"] * r["ny"] * r["nz"] for p, r in zip(polls, reqs))
@@ -622,6 +664,8 @@ def run_served(args, lbmfug):
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
             "latency_over": "converged requests",
             "wall_s": t1 - t0, "solves_per_s": len(conv) / (t1 - t0),
+            "arrival_rate_per_s": args.serve_rate / float(np.mean([r["arrival_gap_s"] for r in reqs])),
+            "gpu_busy_pct": busy_pct,
             "nc_node_steps_per_s": work / (t1 - t0), "slots": args.serve_slots,
             "peak_bytes": stats["peak_bytes"], "budget_bytes": stats["budget_bytes"], "rounds": stats["rounds"],
             "precision": "fp32dev (binary32 populations; thermodynamics double-binary32 on D2Q9, binary64 on D3Q19)",
@@ -682,6 +726,7 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-max-steps", type=int, default=200000)
     ap.add_argument("--serve-fp64-s", type=float, default=60.0, help="seconds of the binary64 one-at-a-time sample")
+    ap.add_argument("--serve-rate", type=float, default=1.0, help="arrival-rate multiplier of the served requests")
     ap.add_argument("--schedule", default="auto", choices=["auto", "threepass", "fused"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

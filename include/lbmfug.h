@@ -156,6 +156,19 @@ int lbm_init_fields_device(lbm_problem *p, const double *d_rho, const double *d_
 int lbm_step(lbm_problem *p, long long n);
 
 /*
+ * The same as lbm_step(p, n), replayed from a CUDA graph: the first call for
+ * a given n (and each of the two state buffers it can start from) captures
+ * the n steps on the handle's stream and instantiates them, later calls
+ * launch the graph.  For loops that advance a problem by the same n again
+ * and again (the served form's rounds), where launching n steps kernel by
+ * kernel would cost more than running them.  The first call synchronises
+ * once if the fused schedule's geometry is not tuned yet; it must not be
+ * made while the handle's stream is being captured by the caller (it then
+ * falls back to lbm_step).  With the mass monitor on it is lbm_step.
+ */
+int lbm_step_graph(lbm_problem *p, long long n);
+
+/*
  * Macroscopic fields of the current state into caller-owned host buffers
  * (any may be NULL): rho[i][...] mass densities; u[d][...] the velocity of
  * the forced step, (sum e g + F/2)/rho; p[...] the PR pressure of Eq. (9) at

@@ -48,6 +48,10 @@ struct lbm_problem {
     bool have_snap = false;
     void *fscratch = nullptr;  // psi / mu scratch of lbm_forces
     float2 *mu = nullptr;      // [nc][N] grad mu_i of the LBM_FP32DEV step (the mu pass writes it)
+    // lbm_step_graph: n steps captured once per starting buffer (cur = 0, 1)
+    long long graph_n = 0;
+    cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
+    long long graph_launches = 0;  // kernels in one replay
     long long launches = 0;
     long long monitor_step = -1;
     double *mon = nullptr;  // [nc] latest monitored mass
@@ -565,6 +569,65 @@ int lbm_step(lbm_problem *p, long long n)
     return LBM_OK;
 }
 
+int lbm_step_graph(lbm_problem *p, long long n)
+{
+    if (!p || n < 1) return LBM_EINVAL;
+    if (!p->initialized) return LBM_ESTATE;
+    if (p->sticky) return p->sticky;
+    if (p->opt.monitor_every > 0) return lbm_step(p, n);  // the monitor's host bookkeeping is per step
+    if (p->fused && !p->tuned) {                          // timing trials cannot run inside a capture
+        const int st = tune_geometry(p);
+        if (st) return p->sticky = st;
+    }
+    if (p->multipass && !p->psi_valid) {                   // psi of the initial state, before the capture
+        if (launch_multipass_psi(p->lattice, p->nc, p->P, p->st[p->cur], p->psi2, p->stream))
+            return p->sticky = LBM_ECUDA;
+        p->launches += 1;
+        p->psi_valid = true;
+    }
+    if (p->graph_n != n) {
+        for (int k = 0; k < 2; ++k)
+            if (p->graph_exec[k]) {
+                cudaGraphExecDestroy(p->graph_exec[k]);
+                p->graph_exec[k] = nullptr;
+            }
+        p->graph_n = n;
+    }
+    const int c = p->cur;
+    if (!p->graph_exec[c]) {
+        const long long steps0 = p->steps, launches0 = p->launches;
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            return lbm_step(p, n);  // the stream cannot be captured (for example, already capturing)
+        }
+        const int st = lbm_step(p, n);
+        const cudaError_t ce = cudaStreamEndCapture(p->stream, &g);
+        // the capture recorded the steps without running them: undo the bookkeeping
+        p->cur = c;
+        p->steps = steps0;
+        p->graph_launches = p->launches - launches0;
+        p->launches = launches0;
+        if (st || ce != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            p->sticky = LBM_OK;
+            return st ? st : LBM_ECUDA;
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&p->graph_exec[c], g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            p->graph_exec[c] = nullptr;
+            return LBM_ECUDA;
+        }
+    }
+    if (cudaGraphLaunch(p->graph_exec[c], p->stream) != cudaSuccess) return p->sticky = LBM_ECUDA;
+    p->launches += p->graph_launches;
+    p->steps += n;
+    if (n % 2) p->cur ^= 1;
+    return LBM_OK;
+}
+
 int lbm_moments_device(lbm_problem *p, double *d_rho, double *d_u, double *d_pressure, double *d_lnf)
 {
     if (!p) return LBM_EINVAL;
@@ -798,6 +861,8 @@ int lbm_destroy(lbm_problem *p)
 {
     if (!p) return LBM_OK;
     if (p->stream) cudaStreamSynchronize(p->stream);
+    for (int k = 0; k < 2; ++k)
+        if (p->graph_exec[k]) cudaGraphExecDestroy(p->graph_exec[k]);
     dev_free_all(p);
     if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
     delete p;

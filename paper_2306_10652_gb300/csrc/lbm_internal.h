@@ -71,8 +71,8 @@ FusedGeom fused_geometry(int prec, int nc, const Params &P, int num_sms, int ext
 FusedGeom fused_geometry_forced(int prec, int nc, const Params &P, int num_sms, int strip, int seg_h);
 // binary64 only: densities of the fused state from the populations
 int launch_fused_density(int prec, int nc, const Params &P, StateBufs st, cudaStream_t s);
-// mu: [nc][N] (hi, lo) chemical potentials of LBM_FP32DEV (else unused);
-// *launches receives the kernels launched.
+// mu: [nc][N] grad mu_i of LBM_FP32DEV (else unused); *launches receives the
+// kernels launched.
 int launch_fused_step(int prec, int nc, const Params &P, const FusedGeom &geo, StateBufs in,
                       StateBufs out, double *mass_partials, float2 *mu, int *launches, cudaStream_t s);
 // Sum the per-CTA mass partials of a monitored fused step into out[nc].

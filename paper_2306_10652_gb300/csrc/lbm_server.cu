@@ -168,7 +168,7 @@ struct lbm_server {
             for (auto &r : active) {
                 const long long n = std::min<long long>(r->check_every, r->max_steps - r->steps);
                 if (n > 0 && !r->error) {
-                    const int st = lbm_step(r->h, n);
+                    const int st = lbm_step_graph(r->h, n);
                     if (st) r->error = st;
                     r->steps += n;
                 }

@@ -58,6 +58,7 @@ _sig("lbm_set_options", ctypes.c_int, _vp, ctypes.POINTER(lbm_options))
 _sig("lbm_init_fields", ctypes.c_int, _vp, _dp, _dp)
 _sig("lbm_init_fields_device", ctypes.c_int, _vp, _vp, _vp)
 _sig("lbm_step", ctypes.c_int, _vp, ctypes.c_longlong)
+_sig("lbm_step_graph", ctypes.c_int, _vp, ctypes.c_longlong)
 _sig("lbm_moments", ctypes.c_int, _vp, _dp, _dp, _dp, _dp)
 _sig("lbm_moments_device", ctypes.c_int, _vp, _vp, _vp, _vp, _vp)
 _sig("lbm_mass", ctypes.c_int, _vp, _dp)
@@ -232,6 +233,10 @@ class Problem:
 
     def step(self, n=1):
         _check(_lib.lbm_step(self._h, int(n)), "lbm_step")
+
+    def step_graph(self, n):
+        """lbm_step_graph: n steps replayed from a captured CUDA graph."""
+        _check(_lib.lbm_step_graph(self._h, int(n)), "lbm_step_graph")
 
     def moments(self, want=("rho", "u", "p", "lnf")):
         out = {}

@@ -331,7 +331,7 @@ def test_launch_geometry_changes_no_result(precision):
     u = synth.random_velocity(320, 2, shape, 1e-3)
     out = []
     for kw in (dict(tune=0), dict(tune=1), dict(strip=37, seg_h=5), dict(strip=100, seg_h=45),
-               dict(strip=7, seg_h=1)):
+               dict(strip=7, seg_h=1), dict(strip=61, seg_h=7)):
         with gpu_problem(c, 0, shape, precision=precision, schedule=FUSED, **kw) as gp:
             gp.init_fields(rho, u)
             gp.step(6)
@@ -341,3 +341,24 @@ def test_launch_geometry_changes_no_result(precision):
                 assert (info["strip"], info["seg_h"]) == (kw["strip"], kw["seg_h"]), info
     for o in out[1:]:
         assert np.array_equal(o, out[0])
+
+
+@pytest.mark.parametrize("precision,schedule,lattice,shape", [
+    (FP32DEV, FUSED, 0, (1, 40, 130)), (FP32, FUSED, 0, (1, 40, 130)), (FP64, FUSED, 0, (1, 12, 30)),
+    (FP32DEV, MULTIPASS, 1, (6, 7, 9)), (FP64, THREEPASS, 1, (4, 5, 6))],
+    ids=["fp32dev-fused", "fp32-fused", "fp64-fused", "fp32dev-multipass-d3q19", "fp64-threepass-d3q19"])
+def test_step_graph_equals_step(precision, schedule, lattice, shape):
+    """lbm_step_graph (the steps captured once into a CUDA graph per starting
+    buffer and replayed) gives bitwise the states of lbm_step, for odd and
+    even step counts and repeated replays."""
+    c = seeded_mixture(330, 3, lattice, shape)
+    rho = smooth_rho(330, c, shape)
+    out = []
+    for graph in (False, True):
+        with gpu_problem(c, lattice, shape, precision=precision, schedule=schedule) as gp:
+            gp.init_fields(rho)
+            for n in (3, 3, 4, 4, 1):
+                (gp.step_graph if graph else gp.step)(n)
+            assert gp.step_count() == 15
+            out.append(gp.get_state())
+    assert np.array_equal(out[0], out[1])
