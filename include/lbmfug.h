@@ -228,6 +228,30 @@ int lbm_monitor(lbm_problem *p, double *mass, long long *at_step, int *nonfinite
 /* Number of kernels this handle has launched (every launch is counted). */
 int lbm_launch_count(const lbm_problem *p, long long *launches);
 
+/* Device time of each kernel of the steps, measured with two CUDA events
+ * recorded on the handle's stream around every launch of lbm_step (the
+ * launch-geometry trials of the first step are not recorded).  Off by
+ * default.  lbm_timing_enable(p, 1) zeroes the counters and starts recording;
+ * lbm_timing_enable(p, 0) stops and discards them (both synchronise the
+ * stream when a timer exists).  While recording, lbm_step_graph runs as
+ * lbm_step, and lbm_step synchronises the stream once per 4096 recorded
+ * launches to read and recycle the events.  Returns LBM_EINVAL (null p, on
+ * not 0 or 1), LBM_ENOMEM, LBM_ECUDA. */
+int lbm_timing_enable(lbm_problem *p, int on);
+
+typedef struct lbm_kernel_time {
+    const char *name;   /* static string naming the kernel (owned by the library) */
+    long long launches; /* launches timed since lbm_timing_enable(p, 1) */
+    double total_ms;    /* sum of their event-to-event times, milliseconds */
+} lbm_kernel_time;
+
+/* Synchronises the handle's stream, then writes one entry per kernel that
+ * has launched since timing was enabled (a fixed order) into out[0 ..
+ * min(max, *n)) and the number of such kernels into *n.  The counters keep
+ * accumulating.  Returns LBM_EINVAL (null p or n, max < 0, out null with
+ * max > 0), LBM_ESTATE (timing not enabled), LBM_ECUDA. */
+int lbm_timing_read(lbm_problem *p, lbm_kernel_time *out, int max, int *n);
+
 /* Raw populations, binary64, layout g[i][a][z][y][x] (post-streaming).
  * *bytes in: capacity of buf; out: bytes needed.  buf NULL = size query. */
 int lbm_get_state(lbm_problem *p, double *buf, size_t *bytes);

@@ -53,6 +53,7 @@ struct lbm_problem {
     cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
     long long graph_launches = 0;  // kernels in one replay
     long long launches = 0;
+    KernelTimer *timer = nullptr;  // lbm_timing_enable: per-kernel CUDA-event timing (null: off)
     long long monitor_step = -1;
     double *mon = nullptr;  // [nc] latest monitored mass
     double *partials = nullptr;
@@ -71,6 +72,93 @@ struct TuneCand {
 std::vector<TuneCand> tune_candidates(const lbm_problem *p);
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ECUDA; }
+
+const char *const kKtNames[kKtSlots] = {
+    "k_mu32 (double-binary32 mu pass)", "k_fused32 / k_fused (fused step kernel)",
+    "k_mass_final (monitored mass)",    "k_mp_psi",
+    "k_mp_mu",                          "k_mp_collide",
+    "k_mp_update",                      "three-pass step (k_macro, k_lap, k_collide, k_rupdate)",
+    "monitor (densities and mass)"};
+
+// Events recorded but not yet read, above which lbm_step synchronises the
+// stream to recycle them.
+constexpr size_t kKtMaxPending = 4096;
+
+}  // namespace
+
+namespace lbmfug {
+
+void KernelTimer::begin(int slot, cudaStream_t s)
+{
+    if (err) return;
+    cudaEvent_t e = nullptr;
+    if (!pool.empty()) {
+        e = pool.back();
+        pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        err = 1;
+        return;
+    }
+    if (cudaEventRecord(e, s) != cudaSuccess) {
+        pool.push_back(e);
+        err = 1;
+        return;
+    }
+    open = slot;
+    open_ev = e;
+}
+
+void KernelTimer::end(cudaStream_t s)
+{
+    if (err || open < 0) return;
+    cudaEvent_t e = nullptr;
+    if (!pool.empty()) {
+        e = pool.back();
+        pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        err = 1;
+        return;
+    }
+    if (cudaEventRecord(e, s) != cudaSuccess) {
+        pool.push_back(e);
+        err = 1;
+        return;
+    }
+    pending.push_back({open, open_ev, e});
+    open = -1;
+    open_ev = nullptr;
+}
+
+int KernelTimer::collect()
+{
+    for (const Rec &r : pending) {
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) err = 1;
+        ms[r.slot] += t;
+        launches[r.slot] += 1;
+        pool.push_back(r.a);
+        pool.push_back(r.b);
+    }
+    pending.clear();
+    return err ? LBM_ECUDA : LBM_OK;
+}
+
+void KernelTimer::release()
+{
+    for (const Rec &r : pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    pending.clear();
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    pool.clear();
+    if (open_ev) cudaEventDestroy(open_ev);
+    open_ev = nullptr;
+}
+
+}  // namespace lbmfug
+
+namespace {
 
 int pstore_bytes(const lbm_problem *p) { return p->opt.precision == LBM_FP64 ? 8 : 4; }
 
@@ -328,7 +416,7 @@ int tune_geometry(lbm_problem *p)
                 if (k == 1) e = (int)cudaEventRecord(e0, p->stream);
                 if (!e)
                     e = launch_fused_step(p->opt.precision, p->nc, p->P, g, p->st[p->cur], p->st[p->cur ^ 1],
-                                          nullptr, p->mu, &nl, p->stream);
+                                          nullptr, p->mu, &nl, nullptr, p->stream);
                 p->launches += nl;
             }
             if (!e) e = (int)cudaEventRecord(e1, p->stream);
@@ -371,6 +459,30 @@ int finish_init(lbm_problem *p)
     p->initialized = true;
     p->sticky = LBM_OK;
     return cuda_status(cudaGetLastError());
+}
+
+// Host validation of the initial fields, branch-free within blocks of 4096
+// values so that the compiler can vectorise it.
+bool all_positive_finite(const double *x, size_t n)
+{
+    for (size_t b = 0; b < n; b += 4096) {
+        const size_t e = std::min(n, b + 4096);
+        int bad = 0;
+        for (size_t k = b; k < e; ++k) bad |= !(x[k] > 0.0 && x[k] <= 1.7976931348623157e308);
+        if (bad) return false;
+    }
+    return true;
+}
+
+bool all_finite(const double *x, size_t n)
+{
+    for (size_t b = 0; b < n; b += 4096) {
+        const size_t e = std::min(n, b + 4096);
+        int bad = 0;
+        for (size_t k = b; k < e; ++k) bad |= !(x[k] >= -1.7976931348623157e308 && x[k] <= 1.7976931348623157e308);
+        if (bad) return false;
+    }
+    return true;
 }
 
 int check_flag(lbm_problem *p)
@@ -483,11 +595,8 @@ int lbm_init_fields(lbm_problem *p, const double *rho, const double *u)
 {
     if (!p || !rho) return LBM_EINVAL;
     const size_t nrho = (size_t)p->nc * p->N;
-    for (size_t k = 0; k < nrho; ++k)
-        if (!(rho[k] > 0.0) || !std::isfinite(rho[k])) return LBM_EINVAL;
-    if (u)
-        for (size_t k = 0; k < (size_t)p->D * p->N; ++k)
-            if (!std::isfinite(u[k])) return LBM_EINVAL;
+    if (!all_positive_finite(rho, nrho)) return LBM_EINVAL;
+    if (u && !all_finite(u, (size_t)p->D * p->N)) return LBM_EINVAL;
     int st = ensure_allocated(p);
     if (st) return st;
     // stage through the three-pass scratch (rho: nc*N doubles; u: lnf buffer holds D*N <= nc*N? no)
@@ -520,30 +629,43 @@ int lbm_step(lbm_problem *p, long long n)
     }
     for (long long s = 0; s < n; ++s) {
         const bool mon = every > 0 && ((p->steps + 1) % every == 0);
-        int e;
+        int e = 0;
+        KernelTimer *kt = p->timer;
+        if (kt && kt->pending.size() >= kKtMaxPending) {
+            if (cudaStreamSynchronize(p->stream) != cudaSuccess || kt->collect()) {
+                p->sticky = LBM_ECUDA;
+                return p->sticky;
+            }
+        }
         if (p->fused) {
             int nl = 0;
             e = launch_fused_step(p->opt.precision, p->nc, p->P, p->geo, p->st[p->cur],
                                   p->st[p->cur ^ 1], mon ? p->mass_partials : nullptr, p->mu, &nl,
-                                  p->stream);
+                                  kt, p->stream);
             p->launches += nl;
             if (!e && mon) {
+                kt_begin(kt, kKtMass, p->stream);
                 e = launch_fused_mass_final(p->nc, p->geo, p->mass_partials, p->mon, p->flag, p->stream);
+                kt_end(kt, p->stream);
                 p->launches += 1;
             }
         } else if (p->multipass) {
             if (!p->psi_valid) {
+                kt_begin(kt, kKtMpPsi, p->stream);
                 e = launch_multipass_psi(p->lattice, p->nc, p->P, p->st[p->cur], p->psi2, p->stream);
+                kt_end(kt, p->stream);
                 p->launches += 1;
                 p->psi_valid = true;
             }
             if (!e)
                 e = launch_multipass_step(p->lattice, p->nc, p->P, p->st[p->cur], p->st[p->cur ^ 1], p->psi2,
-                                          p->mu, p->w.osum, p->w.ocmp, p->stream);
+                                          p->mu, p->w.osum, p->w.ocmp, kt, p->stream);
             p->launches += 3;
         } else {
+            kt_begin(kt, kKtThreePass, p->stream);
             e = launch_threepass_step(p->lattice, sprec(p), p->nc, p->P, p->st[p->cur],
                                       p->st[p->cur ^ 1], p->w, p->stream);
+            kt_end(kt, p->stream);
             p->launches += threepass_launches_per_step(p->lattice, sprec(p), p->nc);
         }
         if (e) {
@@ -555,9 +677,11 @@ int lbm_step(lbm_problem *p, long long n)
         if (mon && !p->fused) {
             // (the multi-pass schedule's psi of the new state stays valid: moments do not touch it)
             // mass of the new state: densities by the first pass of the next step's kernels
+            kt_begin(kt, kKtMonitor, p->stream);
             e = launch_fields(p->lattice, sprec(p), p->nc, p->P, p->st[p->cur], p->w, p->w.rho,
                               nullptr, nullptr, nullptr, p->stream);
             if (!e) e = launch_mass(p->nc, p->N, p->w.rho, p->partials, p->mon, p->flag, p->stream);
+            kt_end(kt, p->stream);
             p->launches += 3;
             if (e) {
                 p->sticky = LBM_ECUDA;
@@ -575,6 +699,7 @@ int lbm_step_graph(lbm_problem *p, long long n)
     if (!p->initialized) return LBM_ESTATE;
     if (p->sticky) return p->sticky;
     if (p->opt.monitor_every > 0) return lbm_step(p, n);  // the monitor's host bookkeeping is per step
+    if (p->timer) return lbm_step(p, n);                  // per-launch events are host bookkeeping too
     if (p->fused && !p->tuned) {                          // timing trials cannot run inside a capture
         const int st = tune_geometry(p);
         if (st) return p->sticky = st;
@@ -652,7 +777,7 @@ int lbm_moments(lbm_problem *p, double *rho, double *u, double *pressure, double
         cudaFree(d_u);
         return LBM_ENOMEM;
     }
-    int st = lbm_moments_device(p, p->w.rho, d_u, d_p, p->w.lnf);
+    int st = lbm_moments_device(p, p->w.rho, d_u, d_p, lnf ? p->w.lnf : nullptr);
     const size_t fb = (size_t)p->nc * nb;
     if (!st && rho && cudaMemcpyAsync(rho, p->w.rho, fb, cudaMemcpyDeviceToHost, p->stream)) st = LBM_ECUDA;
     if (!st && lnf && cudaMemcpyAsync(lnf, p->w.lnf, fb, cudaMemcpyDeviceToHost, p->stream)) st = LBM_ECUDA;
@@ -832,6 +957,43 @@ int lbm_monitor(lbm_problem *p, double *mass, long long *at_step, int *nonfinite
     return LBM_OK;
 }
 
+int lbm_timing_enable(lbm_problem *p, int on)
+{
+    if (!p || on < 0 || on > 1) return LBM_EINVAL;
+    if (p->timer) {
+        if (p->stream && cudaStreamSynchronize(p->stream) != cudaSuccess) return LBM_ECUDA;
+        p->timer->release();
+        delete p->timer;
+        p->timer = nullptr;
+    }
+    if (on) {
+        p->timer = new (std::nothrow) KernelTimer();
+        if (!p->timer) return LBM_ENOMEM;
+    }
+    return LBM_OK;
+}
+
+int lbm_timing_read(lbm_problem *p, lbm_kernel_time *out, int max, int *n)
+{
+    if (!p || !n || max < 0 || (max > 0 && !out)) return LBM_EINVAL;
+    *n = 0;
+    if (!p->timer) return LBM_ESTATE;
+    if (p->stream && cudaStreamSynchronize(p->stream) != cudaSuccess) return LBM_ECUDA;
+    const int st = p->timer->collect();
+    int k = 0;
+    for (int s = 0; s < kKtSlots; ++s) {
+        if (p->timer->launches[s] == 0) continue;
+        if (k < max) {
+            out[k].name = kKtNames[s];
+            out[k].launches = p->timer->launches[s];
+            out[k].total_ms = p->timer->ms[s];
+        }
+        ++k;
+    }
+    *n = k;
+    return st;
+}
+
 int lbm_launch_count(const lbm_problem *p, long long *launches)
 {
     if (!p || !launches) return LBM_EINVAL;
@@ -863,6 +1025,10 @@ int lbm_destroy(lbm_problem *p)
     if (p->stream) cudaStreamSynchronize(p->stream);
     for (int k = 0; k < 2; ++k)
         if (p->graph_exec[k]) cudaGraphExecDestroy(p->graph_exec[k]);
+    if (p->timer) {
+        p->timer->release();
+        delete p->timer;
+    }
     dev_free_all(p);
     if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
     delete p;

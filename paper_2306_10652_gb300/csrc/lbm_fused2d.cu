@@ -130,10 +130,11 @@ int launch_fused_density(int prec, int nc, const Params &P, StateBufs st, cudaSt
 }
 
 int launch_fused_step(int prec, int nc, const Params &P, const FusedGeom &geo, StateBufs in,
-                      StateBufs out, double *mass_partials, float2 *mu, int *launches, cudaStream_t s)
+                      StateBufs out, double *mass_partials, float2 *mu, int *launches, KernelTimer *kt,
+                      cudaStream_t s)
 {
     const fz::Ops *o = lookup(prec, nc);
-    return o ? o->step(P, geo, in, out, mass_partials, mu, launches, s) : (int)cudaErrorInvalidValue;
+    return o ? o->step(P, geo, in, out, mass_partials, mu, launches, kt, s) : (int)cudaErrorInvalidValue;
 }
 
 int launch_fused_mass_final(int nc, const FusedGeom &geo, const double *partials, double *out,

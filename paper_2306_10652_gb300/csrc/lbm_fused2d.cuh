@@ -816,7 +816,7 @@ struct Ops {
     // one step; mu: the gradient buffer of the double-binary32 chemical
     // potentials, [nc][N] (d/dx, d/dy) (LBM_FP32DEV), else unused.  Returns the launches made through *launches.
     int (*step)(const Params &, const FusedGeom &, StateBufs, StateBufs, double *, float2 *mu, int *launches,
-                cudaStream_t);
+                KernelTimer *, cudaStream_t);
     size_t (*smem)(int W);
     int (*occupancy)(size_t smem);
     int (*occupancy_mu)();  // CTAs per SM of the mu pass (0: the form has none)
@@ -881,30 +881,36 @@ template <int NC, typename S, typename E> struct Impl {
         }
     }
     static int step(const Params &P, const FusedGeom &g, StateBufs in, StateBufs out, double *mp, float2 *mu,
-                    int *launches, cudaStream_t s)
+                    int *launches, KernelTimer *kt, cudaStream_t s)
     {
         dim3 grid(g.nstrips, g.segs);
         const bool small = (long long)NC * 8 * P.N < (1LL << 31);
         *launches = 1;
         if constexpr (k64) {
+            kt_begin(kt, kKtStep, s);
             k_fused<NC, double, double><<<grid, kT, g.smem, s>>>(
                 P, g.strip, g.seg_h, (const double *)in.g, (double *)out.g, in.rhi_d(),
                 out.rhi_d(), mp);
+            kt_end(kt, s);
         } else {
             if constexpr (kDF) {
                 if (!mu) return (int)cudaErrorInvalidValue;
                 dim3 mgrid(g.mnstrips, g.msegs);
                 const size_t b = SmemMu<NC>::bytes();
+                kt_begin(kt, kKtMuPass, s);
                 if (small)
                     k_mu32<NC, int><<<mgrid, kT, b, s>>>(P, g.mstrip, g.mseg_h, in, mu);
                 else
                     k_mu32<NC, long long><<<mgrid, kT, b, s>>>(P, g.mstrip, g.mseg_h, in, mu);
+                kt_end(kt, s);
                 *launches = 2;
             }
+            kt_begin(kt, kKtStep, s);
             if (small)
                 k_fused32<NC, E, int><<<grid, kT, g.smem, s>>>(P, g.strip, g.seg_h, in, out, mp, mu);
             else
                 k_fused32<NC, E, long long><<<grid, kT, g.smem, s>>>(P, g.strip, g.seg_h, in, out, mp, mu);
+            kt_end(kt, s);
         }
         return (int)cudaGetLastError();
     }

@@ -4,9 +4,53 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "lbm_core.cuh"
 
 namespace lbmfug {
+
+// Optional CUDA-event timing of the kernels of a step (lbm_timing_enable /
+// lbm_timing_read): a launch site records an event before and after its
+// launch on the launching stream.  A null timer records nothing.
+enum KtSlot : int {
+    kKtMuPass = 0,   // k_mu32: double-binary32 chemical potentials and their gradients
+    kKtStep,         // k_fused32 / k_fused: the fused step kernel
+    kKtMass,         // k_mass_final: monitored mass of a fused step
+    kKtMpPsi,        // k_mp_psi
+    kKtMpMu,         // k_mp_mu
+    kKtMpCollide,    // k_mp_collide
+    kKtMpUpdate,     // k_mp_update
+    kKtThreePass,    // the three-pass step (k_macro, k_lap, k_collide, k_rupdate)
+    kKtMonitor,      // densities and mass of a monitored multi- or three-pass step
+    kKtSlots
+};
+struct KernelTimer {
+    struct Rec {
+        int slot;
+        cudaEvent_t a, b;
+    };
+    std::vector<cudaEvent_t> pool;  // recycled events
+    std::vector<Rec> pending;       // recorded, not yet read
+    long long launches[kKtSlots] = {};
+    double ms[kKtSlots] = {};
+    int open = -1;  // slot between begin and end
+    cudaEvent_t open_ev = nullptr;
+    int err = 0;    // a CUDA error met while recording
+    void begin(int slot, cudaStream_t s);
+    void end(cudaStream_t s);
+    // read every pending pair (their stream has completed) and recycle the events
+    int collect();
+    void release();
+};
+inline void kt_begin(KernelTimer *t, int slot, cudaStream_t s)
+{
+    if (t) t->begin(slot, s);
+}
+inline void kt_end(KernelTimer *t, cudaStream_t s)
+{
+    if (t) t->end(s);
+}
 
 // Device state of one time level.
 //  binary64 storage: g = all Q populations [nc][Q][N] (double); the fused
@@ -74,7 +118,8 @@ int launch_fused_density(int prec, int nc, const Params &P, StateBufs st, cudaSt
 // mu: [nc][N] grad mu_i of LBM_FP32DEV (else unused); *launches receives the
 // kernels launched.
 int launch_fused_step(int prec, int nc, const Params &P, const FusedGeom &geo, StateBufs in,
-                      StateBufs out, double *mass_partials, float2 *mu, int *launches, cudaStream_t s);
+                      StateBufs out, double *mass_partials, float2 *mu, int *launches, KernelTimer *kt,
+                      cudaStream_t s);
 // Sum the per-CTA mass partials of a monitored fused step into out[nc].
 int launch_fused_mass_final(int nc, const FusedGeom &geo, const double *partials, double *out,
                             int *nonfinite, cudaStream_t s);
@@ -85,7 +130,7 @@ int launch_fused_mass_final(int nc, const FusedGeom &geo, const double *partials
 bool multipass_supported(int lat, int prec, int nc, long long N);
 int launch_multipass_psi(int lat, int nc, const Params &P, StateBufs st, float2 *psi, cudaStream_t s);
 int launch_multipass_step(int lat, int nc, const Params &P, StateBufs in, StateBufs out, float2 *psi,
-                          float2 *mu, float *osum, float *ocmp, cudaStream_t s);
+                          float2 *mu, float *osum, float *ocmp, KernelTimer *kt, cudaStream_t s);
 
 // Chemical potentials and forces of a D2Q9 state from its binary64 densities
 // (lbm_fields_*.cu).  prec: 0 binary64, 1 double-binary32, 2 binary32

@@ -34,10 +34,10 @@ int launch_multipass_psi(int lat, int nc, const Params &P, StateBufs st, float2 
 }
 
 int launch_multipass_step(int lat, int nc, const Params &P, StateBufs in, StateBufs out, float2 *psi,
-                          float2 *mu, float *osum, float *ocmp, cudaStream_t s)
+                          float2 *mu, float *osum, float *ocmp, KernelTimer *kt, cudaStream_t s)
 {
     const mp::Ops *o = lookup(lat, nc);
-    return o ? o->step(P, in, out, psi, mu, osum, ocmp, s) : (int)cudaErrorInvalidValue;
+    return o ? o->step(P, in, out, psi, mu, osum, ocmp, kt, s) : (int)cudaErrorInvalidValue;
 }
 
 }  // namespace lbmfug

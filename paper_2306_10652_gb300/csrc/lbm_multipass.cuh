@@ -267,7 +267,7 @@ inline unsigned grid_for(long long n)
 struct Ops {
     int (*psi)(const Params &, StateBufs, float2 *, cudaStream_t);
     int (*step)(const Params &, StateBufs, StateBufs, float2 *psi, float2 *mu, float *osum, float *ocmp,
-                cudaStream_t);
+                KernelTimer *, cudaStream_t);
 };
 
 template <int LAT, int NC> struct Impl {
@@ -277,16 +277,22 @@ template <int LAT, int NC> struct Impl {
         return (int)cudaGetLastError();
     }
     static int step(const Params &P, StateBufs in, StateBufs out, float2 *ps, float2 *mu, float *osum,
-                    float *ocmp, cudaStream_t s)
+                    float *ocmp, KernelTimer *kt, cudaStream_t s)
     {
         const unsigned G = grid_for(P.N);
         const size_t sm = mp_mu_smem<NC>();
         if (sm > 48 * 1024 &&
             cudaFuncSetAttribute(k_mp_mu<LAT, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
             return (int)cudaGetLastError();
+        kt_begin(kt, kKtMpMu, s);
         k_mp_mu<LAT, NC><<<G, kThreads, sm, s>>>(P, in, ps, mu);
+        kt_end(kt, s);
+        kt_begin(kt, kKtMpCollide, s);
         k_mp_collide<LAT, NC><<<G, kThreads, 0, s>>>(P, in, out, mu, osum, ocmp);
+        kt_end(kt, s);
+        kt_begin(kt, kKtMpUpdate, s);
         k_mp_update<LAT, NC><<<G, kThreads, 0, s>>>(P, in, out, osum, ocmp, ps);
+        kt_end(kt, s);
         return (int)cudaGetLastError();
     }
 };

@@ -118,7 +118,8 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-template <int LAT, int NC, typename S>
+// kRhoOnly: the densities alone (lbm_moments asked for nothing else), no EOS
+template <int LAT, int NC, typename S, bool kRhoOnly = false>
 __global__ void __launch_bounds__(kThreads)
     k_macro(const Params P, StateBufs st, double *__restrict__ rho, double *__restrict__ lnf,
             double *__restrict__ psi, double *__restrict__ jm, double *__restrict__ pout)
@@ -133,6 +134,10 @@ __global__ void __launch_bounds__(kThreads)
         double j[3] = {0.0, 0.0, 0.0};
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
+            if constexpr (kRhoOnly && sizeof(S) == 4) {
+                rho[i * N + r] = (double)st.rhi_f()[i * N + r] + (double)st.rlo[i * N + r];
+                continue;
+            }
             S s = 0, ji[3] = {0, 0, 0};
 #pragma unroll
             for (int a = 0; a < L::Q; ++a) {
@@ -152,6 +157,7 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
             for (int d = 0; d < L::D; ++d) j[d] += (double)ji[d];
         }
+        if constexpr (kRhoOnly) continue;
         double lf[NC], p;
         pr_lnf<NC>(P, rm, lf, &p);
         double ps = 0.0;
@@ -393,7 +399,10 @@ template <int LAT, int NC, typename S> struct Impl {
                       double *u, double *p, double *lnf, cudaStream_t s)
     {
         const unsigned G = grid_for(P.N);
-        k_macro<LAT, NC, S><<<G, kThreads, 0, s>>>(P, st, w.rho, w.lnf, w.psi, w.jm, p);
+        if (!u && !p && !lnf)
+            k_macro<LAT, NC, S, true><<<G, kThreads, 0, s>>>(P, st, w.rho, nullptr, nullptr, nullptr, nullptr);
+        else
+            k_macro<LAT, NC, S><<<G, kThreads, 0, s>>>(P, st, w.rho, w.lnf, w.psi, w.jm, p);
         if (u) {
             k_lap<LAT><<<G, kThreads, 0, s>>>(P, w.psi, w.lap);
             k_collide<LAT, NC, S, false><<<G, kThreads, 0, s>>>(P, st, StateBufs{}, w.rho, w.lnf,

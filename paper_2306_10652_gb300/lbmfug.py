@@ -70,6 +70,14 @@ _sig("lbm_set_state", ctypes.c_int, _vp, _dp, ctypes.c_size_t)
 _sig("lbm_step_count", ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_longlong))
 _sig("lbm_monitor", ctypes.c_int, _vp, _dp, ctypes.POINTER(ctypes.c_longlong), _ip)
 _sig("lbm_launch_count", ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_longlong))
+
+
+class lbm_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_longlong), ("total_ms", ctypes.c_double)]
+
+
+_sig("lbm_timing_enable", ctypes.c_int, _vp, ctypes.c_int)
+_sig("lbm_timing_read", ctypes.c_int, _vp, ctypes.POINTER(lbm_kernel_time), ctypes.c_int, _ip)
 _sig("lbm_field_sums_noalloc", ctypes.c_int, _vp, ctypes.c_int, ctypes.c_longlong, _vp, _vp, _vp)
 class lbm_job(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("T", ctypes.c_double), ("rho", _dp)]
@@ -109,7 +117,8 @@ _sig("lbm_strerror", ctypes.c_char_p, ctypes.c_int)
 EXPORTED = ["lbm_options_default", "lbm_create", "lbm_set_options", "lbm_init_fields",
             "lbm_init_fields_device", "lbm_step", "lbm_moments", "lbm_moments_device", "lbm_mass",
             "lbm_convergence", "lbm_get_state", "lbm_set_state", "lbm_step_count", "lbm_monitor",
-            "lbm_launch_count", "lbm_field_sums_noalloc", "lbm_batch_create", "lbm_batch_run",
+            "lbm_launch_count", "lbm_timing_enable", "lbm_timing_read", "lbm_step_graph",
+            "lbm_forces", "lbm_schedule_info", "lbm_field_sums_noalloc", "lbm_batch_create", "lbm_batch_run",
             "lbm_batch_job_state", "lbm_batch_info", "lbm_batch_set_threads", "lbm_batch_destroy",
             "lbm_server_estimate_bytes", "lbm_server_create", "lbm_server_submit", "lbm_server_poll",
             "lbm_server_result", "lbm_server_wait_all", "lbm_server_stats", "lbm_server_destroy",
@@ -238,12 +247,26 @@ class Problem:
         """lbm_step_graph: n steps replayed from a captured CUDA graph."""
         _check(_lib.lbm_step_graph(self._h, int(n)), "lbm_step_graph")
 
-    def moments(self, want=("rho", "u", "p", "lnf")):
+    def moments(self, want=("rho", "u", "p", "lnf"), out_arrays=None):
+        """lbm_moments of the fields in `want`; out_arrays may give float64
+        C-contiguous host arrays (for example pinned) to write them into."""
         out = {}
-        rho = np.empty((self.nc,) + self.shape) if "rho" in want else None
-        u = np.empty((self.D,) + self.shape) if "u" in want else None
-        p = np.empty(self.shape) if "p" in want else None
-        lnf = np.empty((self.nc,) + self.shape) if "lnf" in want else None
+        given = out_arrays or {}
+
+        def buf(name, shape):
+            if name not in want:
+                return None
+            if name in given:
+                a = given[name]
+                if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != int(np.prod(shape)):
+                    raise ValueError(f"out_arrays[{name!r}]: float64 C-contiguous with {int(np.prod(shape))} values")
+                return a.reshape(shape)
+            return np.empty(shape)
+
+        rho = buf("rho", (self.nc,) + self.shape)
+        u = buf("u", (self.D,) + self.shape)
+        p = buf("p", self.shape)
+        lnf = buf("lnf", (self.nc,) + self.shape)
         _check(_lib.lbm_moments(self._h, _hp(rho), _hp(u), _hp(p), _hp(lnf)), "lbm_moments")
         for k, v in (("rho", rho), ("u", u), ("p", p), ("lnf", lnf)):
             if v is not None:
@@ -300,6 +323,17 @@ class Problem:
         v = ctypes.c_longlong()
         _check(_lib.lbm_launch_count(self._h, ctypes.byref(v)), "lbm_launch_count")
         return v.value
+
+    def timing_enable(self, on=True):
+        """lbm_timing_enable: CUDA events around every kernel launch of lbm_step."""
+        _check(_lib.lbm_timing_enable(self._h, 1 if on else 0), "lbm_timing_enable")
+
+    def timing_read(self):
+        """lbm_timing_read: {kernel name: (launches, total ms)} since timing was enabled."""
+        buf = (lbm_kernel_time * 16)()
+        n = ctypes.c_int()
+        _check(_lib.lbm_timing_read(self._h, buf, 16, ctypes.byref(n)), "lbm_timing_read")
+        return {buf[k].name.decode(): (int(buf[k].launches), float(buf[k].total_ms)) for k in range(min(n.value, 16))}
 
     def step_count(self):
         v = ctypes.c_longlong()

@@ -114,3 +114,22 @@ def test_strerror_and_lattice_tables(lib):
         for k in range(1, Q, 2):
             assert (e[k] == -e[k + 1]).all()
         assert len({tuple(v) for v in e}) == Q
+
+
+def test_timing_arguments_and_states(lib):
+    p = lib.Problem(0, 4, 4, 1, [0.04], [0.1], [0.1], None, 0.06, 1.0)
+    buf = (lib.lbm_kernel_time * 4)()
+    n = ctypes.c_int(7)
+    # reading before enabling is a state error; bad arguments are rejected
+    assert lib._lib.lbm_timing_read(p._h, buf, 4, ctypes.byref(n)) == lib.LBM_ESTATE
+    assert n.value == 0
+    assert lib._lib.lbm_timing_enable(p._h, 2) == lib.LBM_EINVAL
+    assert lib._lib.lbm_timing_enable(None, 1) == lib.LBM_EINVAL
+    assert lib._lib.lbm_timing_read(p._h, None, 4, ctypes.byref(n)) == lib.LBM_EINVAL
+    assert lib._lib.lbm_timing_read(p._h, buf, -1, ctypes.byref(n)) == lib.LBM_EINVAL
+    # enabled before any step: nothing has launched yet
+    p.timing_enable(True)
+    assert p.timing_read() == {}
+    p.timing_enable(False)
+    assert lib._lib.lbm_timing_read(p._h, buf, 4, ctypes.byref(n)) == lib.LBM_ESTATE
+    p.close()

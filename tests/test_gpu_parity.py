@@ -362,3 +362,57 @@ def test_step_graph_equals_step(precision, schedule, lattice, shape):
             assert gp.step_count() == 15
             out.append(gp.get_state())
     assert np.array_equal(out[0], out[1])
+
+
+
+@pytest.mark.parametrize("precision,schedule,lattice,shape,kernels", [
+    (FP32DEV, FUSED, 0, (1, 40, 130), ("k_mu32", "k_fused32")),
+    (FP32, FUSED, 0, (1, 40, 130), ("k_fused32",)),
+    (FP32DEV, MULTIPASS, 1, (10, 12, 14), ("k_mp_mu", "k_mp_collide", "k_mp_update"))],
+    ids=["fp32dev-fused", "fp32-fused", "fp32dev-multipass-d3q19"])
+def test_kernel_timing(precision, schedule, lattice, shape, kernels):
+    """lbm_timing_*: one event pair per launch of every kernel of the step
+    (8 steps: 6 by lbm_step, 2 by lbm_step_graph, which runs as lbm_step while
+    timing), a positive time for each, nothing else recorded, and the same
+    state as without timing."""
+    c = seeded_mixture(331, 3, lattice, shape)
+    rho = smooth_rho(331, c, shape)
+    out = []
+    for timed in (False, True):
+        with gpu_problem(c, lattice, shape, precision=precision, schedule=schedule) as gp:
+            gp.init_fields(rho)
+            gp.step(1)  # the first step times the launch geometries (not recorded)
+            if timed:
+                gp.timing_enable(True)
+            gp.step(6)
+            gp.step_graph(2)
+            if timed:
+                t = gp.timing_read()
+                assert len(t) == len(kernels), t
+                for k in kernels:
+                    launches, ms = next(v for n, v in t.items() if n.startswith(k))
+                    assert launches == 8 and ms > 0.0, (k, t)
+                gp.timing_enable(False)
+            out.append(gp.get_state())
+    assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("precision,schedule,lattice,shape", [
+    (FP32DEV, FUSED, 0, (1, 20, 30)), (FP64, FUSED, 0, (1, 12, 30)), (FP64, THREEPASS, 1, (4, 5, 6)),
+    (FP32DEV, MULTIPASS, 1, (4, 5, 6))],
+    ids=["fp32dev-fused", "fp64-fused", "fp64-threepass-d3q19", "fp32dev-multipass-d3q19"])
+def test_density_only_moments(precision, schedule, lattice, shape):
+    """lbm_moments with only rho requested (the densities-only kernel, no
+    equation of state) returns the densities of the full request bitwise,
+    also into a caller's array."""
+    c = seeded_mixture(332, 3, lattice, shape)
+    rho = smooth_rho(332, c, shape)
+    with gpu_problem(c, lattice, shape, precision=precision, schedule=schedule) as gp:
+        gp.init_fields(rho)
+        gp.step(5)
+        full = gp.moments()["rho"]
+        only = gp.moments(("rho",))["rho"]
+        into = np.empty(full.size)
+        gp.moments(("rho",), out_arrays={"rho": into})
+    assert np.array_equal(full, only)
+    assert np.array_equal(full.reshape(-1), into)
