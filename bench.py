@@ -128,7 +128,8 @@ class ClockSampler:
 
 
 class BusySampler:
-    """nvidia-smi utilization.gpu (percent of time a kernel ran) every 200 ms."""
+    """nvidia-smi utilization.gpu (percent of time a kernel ran) and memory.used
+    (MiB) every 200 ms."""
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
@@ -139,7 +140,7 @@ class BusySampler:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.out = open(self.path, "w")
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", "--query-gpu=utilization.gpu",
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", "--query-gpu=utilization.gpu,memory.used",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=self.out, stderr=subprocess.DEVNULL)
         except Exception:
@@ -147,6 +148,7 @@ class BusySampler:
         return self
 
     def __exit__(self, *exc):
+        self.util, self.mem = [], []
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -154,18 +156,22 @@ class BusySampler:
             except Exception:
                 self.proc.kill()
             self.out.close()
+            for line in open(self.path):
+                try:
+                    u, m = line.split(",")[:2]
+                    self.util.append(float(u))
+                    self.mem.append(float(m))
+                except ValueError:
+                    pass
+            os.unlink(self.path)
 
     def mean(self):
-        if self.proc is None:
-            return None
-        vals = []
-        for line in open(self.path):
-            try:
-                vals.append(float(line.strip()))
-            except ValueError:
-                pass
-        os.unlink(self.path)
-        return statistics.mean(vals) if vals else None
+        """Mean utilization (percent), None without samples."""
+        return statistics.mean(self.util) if self.util else None
+
+    def peak_mem_mib(self):
+        """Largest device memory in use (MiB), None without samples."""
+        return max(self.mem) if self.mem else None
 
 
 def aggregate_replicas(ms, units, world_size, device="cpu"):
@@ -264,6 +270,7 @@ def run_gpu(args):
     cpu = cpu_baseline(case, nx, ny, rho) if (ws == 1 and not args.no_cpu_baseline) else None
     batched = run_batched(args, lbmfug, local) if not args.no_batched else None
     served = run_served(args, lbmfug) if not args.no_served else None
+    served_scale = run_served_scale(args, lbmfug) if not (args.no_served or args.no_serve_scale) else None
     forms = None
     if not args.no_forms:
         forms = {}
@@ -304,6 +311,7 @@ def run_gpu(args):
         "forms": forms,
         "batched": batched,
         "served": served,
+        "served_at_scale": served_scale,
         "gpu_launches": launches,
         "mass_monitor": {"at_step": at, "nonfinite": nonfinite,
                          "mass": None if mass is None else [float(v) for v in mass]},
@@ -391,13 +399,13 @@ def run_e2e(args, lbmfug, case, rho, nx, ny, prec, sched, local):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     prob.init_fields(h_in)
-    prob.step(args.steps)
+    prob.step(args.e2e_steps)
     prob.moments(("rho",), out_arrays={"rho": h_out})
     t1 = time.perf_counter()
     prob.close()
     wall = t1 - t0
-    return {"value": nc * N * args.steps / wall / 1e9, "unit": METRIC,
-            "h2d_bytes_per_step": nc * N * 8 / args.steps, "d2h_bytes_per_step": nc * N * 8 / args.steps,
+    return {"value": nc * N * args.e2e_steps / wall / 1e9, "unit": METRIC, "steps": args.e2e_steps,
+            "h2d_bytes_per_step": nc * N * 8 / args.e2e_steps, "d2h_bytes_per_step": nc * N * 8 / args.e2e_steps,
             "wall_s": wall}
 
 
@@ -685,10 +693,74 @@ def run_served(args, lbmfug):
             "gpu_busy_pct": busy_pct,
             "nc_node_steps_per_s": work / (t1 - t0), "slots": args.serve_slots,
             "peak_bytes": stats["peak_bytes"], "budget_bytes": stats["budget_bytes"], "rounds": stats["rounds"],
-            "precision": "fp32dev (binary32 populations; thermodynamics double-binary32 on D2Q9, binary64 on D3Q19)",
+            "precision": "fp32dev (binary32 populations; thermodynamics double-binary32: fused D2Q9, "
+                         "multi-pass D3Q19)",
             "fp64_one_at_a_time": {"measured": True, "solves": solved64, "wall_s": w64,
                                    "solves_per_s": solved64 / w64 if w64 > 0 else None,
                                    "sample": "requests in a seeded random order, each alone to the criterion"}}
+
+
+def scale_field(r, n_x, shape, W):
+    """Eq. (15) slab along x of one request at another size: the profile
+    along x broadcast over y and z (molar densities [Nc][nz][ny][nx])."""
+    SV = r["S_V"]
+    rv = np.asarray(r["rhoi_V"])[:, None]
+    rl = np.asarray(r["rhoi_L"])[:, None]
+    x = np.arange(n_x, dtype=float)[None, :]
+    prof = rv + 0.5 * (rl - rv) * (np.tanh(2 * (x - 0.5 * SV * n_x) / W) - np.tanh(2 * (x - (1 - 0.5 * SV) * n_x) / W))
+    return np.ascontiguousarray(np.broadcast_to(prof[:, None, None, :], (prof.shape[0],) + tuple(shape)))
+
+
+def run_served_scale(args, lbmfug):
+    """The served form at the largest geometries of the served configuration:
+    D3Q19 slab boxes of 160^3-192^3 and D2Q9 slabs of 1024^2, with the
+    mixtures of the served request set (Nc 2..10), every request run for a
+    fixed number of steps (boxes this size relax over millions of steps, so
+    they are not run to convergence).  All are submitted at once, so the 80 %
+    memory budget, not the slot count, decides how many run together."""
+    import torch
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    d = json.load(open(SERVE_FILE))
+    r3 = [r for r in d["requests"] if r["lattice"] == 1]
+    r2 = [r for r in d["requests"] if r["lattice"] == 0]
+    plan = [(1, r, (n, n, n)) for n in (192, 192, 176, 176, 160, 160) for r in r3]
+    plan += [(0, r, (1, 1024, 1024)) for r in r2[:args.scale_2d]]
+    steps, every = args.scale_steps, max(1, args.scale_steps // 2)
+    est = [lbmfug.lbm_server_estimate_bytes(lat, sh[2], sh[1], sh[0], r["nc"], lbmfug.LBM_FP32DEV)
+           for lat, r, sh in plan]
+    with lbmfug.Server(0.8, max_active=len(plan)) as srv, BusySampler(0) as busy:
+        t0 = time.perf_counter()
+        ids = []
+        for lat, r, sh in plan:
+            rho = scale_field(r, sh[2], sh, d["W"])
+            ids.append(srv.submit(lat, r["a"], r["b"], r["omega"], np.asarray(r["kij"]), r["T"], d["tau"], rho,
+                                  precision=lbmfug.LBM_FP32DEV, check_every=every, max_steps=steps, tol=0.0,
+                                  kappa_ref=d["kappa_ref"]))
+            del rho
+        t_sub = time.perf_counter() - t0
+        srv.wait_all()
+        t1 = time.perf_counter()
+        polls = [srv.poll(j) for j in ids]
+        times = [srv.times(j) for j in ids]
+        stats = srv.stats()
+        adm = srv.admission()
+    work = sum(p["steps"] * r["nc"] * sh[0] * sh[1] * sh[2] for p, (lat, r, sh) in zip(polls, plan))
+    q = np.array([t[0] for t in times])
+    run = np.array([t[1] for t in times])
+    return {"requests": len(plan),
+            "geometries": f"{len([1 for p in plan if p[0] == 1])} D3Q19 boxes 160^3-192^3, "
+                          f"{len([1 for p in plan if p[0] == 0])} D2Q9 1024^2; Nc of the served mixtures",
+            "steps_per_request": steps, "finished": sum(p["state"] == "exhausted" for p in polls),
+            "failed": sum(p["state"] == "failed" for p in polls),
+            "estimated_bytes_all": float(sum(est)), "budget_bytes": stats["budget_bytes"],
+            "peak_bytes": stats["peak_bytes"], "peak_active": adm["peak_active"],
+            "memory_waits": adm["memory_waits"], "device_mem_peak_mib": busy.peak_mem_mib(),
+            "wall_s": t1 - t0, "submit_s": t_sub, "nc_node_steps_per_s": work / (t1 - t0),
+            "queued_s": {"p50": float(np.percentile(q, 50)), "max": float(q.max())},
+            "run_s": {"p50": float(np.percentile(run, 50)), "max": float(run.max())},
+            "gpu_busy_pct": busy.mean(),
+            "precision": "fp32dev (multi-pass D3Q19, fused D2Q9)"}
 
 
 def run_reference(args):
@@ -705,7 +777,7 @@ def run_reference(args):
     for _ in range(args.warmup):
         oracle_rate(case, rho, crop, 1, 0)
     _, dt1, used = oracle_rate(case, rho, crop, 1, 0)
-    per_step_s = max(0.5, 60.0 / max(args.steps, 1))
+    per_step_s = max(0.1, 60.0 / max(args.steps, 1))
     inner = max(1, int(per_step_s / max(dt1, 1e-3)))
     t0 = time.perf_counter()
     for _ in range(args.steps):
@@ -727,7 +799,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--nc", type=int, default=10)
@@ -735,6 +807,8 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the comparison forms")
     ap.add_argument("--grid", default=None, help="NXxNY override of the workload grid (profiling)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=40, help="steps of the end-to-end job (init from host, steps, "
+                                                               "densities to host)")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-jobs", type=int, default=None, help="first N jobs of the sweep")
     ap.add_argument("--batch-max-steps", type=int, default=1000000)
@@ -744,6 +818,9 @@ def main():
     ap.add_argument("--serve-max-steps", type=int, default=200000)
     ap.add_argument("--serve-fp64-s", type=float, default=60.0, help="seconds of the binary64 one-at-a-time sample")
     ap.add_argument("--serve-rate", type=float, default=1.0, help="arrival-rate multiplier of the served requests")
+    ap.add_argument("--no-serve-scale", action="store_true", help="skip the served form at the largest geometries")
+    ap.add_argument("--scale-steps", type=int, default=200, help="steps per request of the served form at scale")
+    ap.add_argument("--scale-2d", type=int, default=8, help="D2Q9 1024^2 requests of the served form at scale")
     ap.add_argument("--schedule", default="auto", choices=["auto", "threepass", "fused"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -397,6 +397,16 @@ int lbm_server_wait_all(lbm_server *s);
 int lbm_server_stats(lbm_server *s, long long *submitted, long long *completed, size_t *peak_bytes,
                      double *budget_bytes, long long *rounds);
 
+/* Admission record: the most requests that ran at once, and the number of
+ * requests that waited at the head of the queue because the memory budget
+ * (not the max_active slots) held them back. */
+int lbm_server_admission(lbm_server *s, int *peak_active, long long *memory_waits);
+
+/* Seconds a finished request (state 2, 3 or 4) spent queued (submission to
+ * start) and running (start to finish).  LBM_ESTATE while it is unfinished,
+ * LBM_EINVAL for an unknown id. */
+int lbm_server_times(lbm_server *s, long long id, double *queued_s, double *run_s);
+
 /* Finish the queued and running requests, then stop the loop. */
 int lbm_server_destroy(lbm_server *s);
 

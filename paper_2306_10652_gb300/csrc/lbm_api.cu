@@ -91,6 +91,13 @@ namespace lbmfug {
 void KernelTimer::begin(int slot, cudaStream_t s)
 {
     if (err) return;
+    if (last_end) {
+        open = slot;
+        open_ev = last_end;
+        open_shared = true;
+        last_end = nullptr;
+        return;
+    }
     cudaEvent_t e = nullptr;
     if (!pool.empty()) {
         e = pool.back();
@@ -106,6 +113,7 @@ void KernelTimer::begin(int slot, cudaStream_t s)
     }
     open = slot;
     open_ev = e;
+    open_shared = false;
 }
 
 void KernelTimer::end(cudaStream_t s)
@@ -124,9 +132,10 @@ void KernelTimer::end(cudaStream_t s)
         err = 1;
         return;
     }
-    pending.push_back({open, open_ev, e});
+    pending.push_back({open, open_ev, e, open_shared});
     open = -1;
     open_ev = nullptr;
+    last_end = e;
 }
 
 int KernelTimer::collect()
@@ -136,24 +145,26 @@ int KernelTimer::collect()
         if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) err = 1;
         ms[r.slot] += t;
         launches[r.slot] += 1;
-        pool.push_back(r.a);
+        if (!r.a_shared) pool.push_back(r.a);
         pool.push_back(r.b);
     }
     pending.clear();
+    last_end = nullptr;
     return err ? LBM_ECUDA : LBM_OK;
 }
 
 void KernelTimer::release()
 {
     for (const Rec &r : pending) {
-        cudaEventDestroy(r.a);
+        if (!r.a_shared) cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
     }
     pending.clear();
     for (cudaEvent_t e : pool) cudaEventDestroy(e);
     pool.clear();
-    if (open_ev) cudaEventDestroy(open_ev);
+    if (open_ev && !open_shared) cudaEventDestroy(open_ev);
     open_ev = nullptr;
+    last_end = nullptr;
 }
 
 }  // namespace lbmfug
@@ -627,6 +638,7 @@ int lbm_step(lbm_problem *p, long long n)
             return st;
         }
     }
+    if (p->timer) p->timer->last_end = nullptr;  // other work may have been enqueued since
     for (long long s = 0; s < n; ++s) {
         const bool mon = every > 0 && ((p->steps + 1) % every == 0);
         int e = 0;

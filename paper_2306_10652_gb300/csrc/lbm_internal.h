@@ -29,6 +29,7 @@ struct KernelTimer {
     struct Rec {
         int slot;
         cudaEvent_t a, b;
+        bool a_shared;  // a is the previous record's b (recycled with that record)
     };
     std::vector<cudaEvent_t> pool;  // recycled events
     std::vector<Rec> pending;       // recorded, not yet read
@@ -36,6 +37,11 @@ struct KernelTimer {
     double ms[kKtSlots] = {};
     int open = -1;  // slot between begin and end
     cudaEvent_t open_ev = nullptr;
+    bool open_shared = false;
+    // The end event of the last timed launch, while nothing else has been
+    // enqueued after it: the next begin() takes it as its start event, so
+    // back-to-back launches cost one event each.  lbm_step clears it on entry.
+    cudaEvent_t last_end = nullptr;
     int err = 0;    // a CUDA error met while recording
     void begin(int slot, cudaStream_t s);
     void end(cudaStream_t s);

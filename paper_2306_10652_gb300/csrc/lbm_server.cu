@@ -41,6 +41,7 @@ struct Request {
     long long max_steps = 0;
     size_t bytes = 0;
     int state = 0;  // 0 queued, 1 running, 2 converged, 3 failed, 4 exhausted (max_steps)
+    bool mem_wait = false;  // waited at the head of the queue for memory while a slot was free
     int error = LBM_OK;
     long long steps = 0;
     double last_drho = 0.0;
@@ -55,9 +56,12 @@ size_t estimate_bytes(int lattice, long long N, int nc, int precision)
     const int D = lattice == LBM_D2Q9 ? 2 : 3;
     const size_t f = (size_t)nc * N;
     size_t b = (precision == LBM_FP64) ? 2 * f * Q * 8 + 2 * f * 8 : 2 * f * ((Q - 1) * 4 + 8) + 2 * f * 4;
+    if (precision != LBM_FP64) b += f * 8 + (size_t)N * 8;  // grad mu (or mu) pairs, psi pairs
     b += 2 * f * 8 + (size_t)N * 8 * (2 + D);  // three-pass scratch fields
     b += f * 8;                                 // convergence snapshot
-    return b + (8u << 20);                      // launch tables, reductions, slack
+    // reductions and launch tables, plus the device allocator's rounding of
+    // each of about twenty buffers to its 2 MiB granule
+    return b + (48u << 20);
 }
 
 }  // namespace
@@ -74,6 +78,8 @@ struct lbm_server {
     bool stop = false;
     size_t active_bytes = 0, peak_bytes = 0;
     long long completed = 0, rounds = 0;
+    int peak_active = 0;         // most jobs running at once
+    long long memory_waits = 0;  // requests held back by the budget with a slot free
     std::thread worker;
 
     void finish(const std::shared_ptr<Request> &r, int state)
@@ -159,6 +165,12 @@ struct lbm_server {
                     active_bytes += r->bytes;
                     if (active_bytes > peak_bytes) peak_bytes = active_bytes;
                     admit.push_back(r);
+                }
+                const int running = (int)(active.size() + admit.size());
+                if (running > peak_active) peak_active = running;
+                if (!queue.empty() && running < max_active && !queue.front()->mem_wait) {
+                    queue.front()->mem_wait = true;
+                    memory_waits += 1;
                 }
             }
             for (auto &r : admit)
@@ -309,6 +321,28 @@ int lbm_server_stats(lbm_server *s, long long *submitted, long long *completed, 
     if (peak_bytes) *peak_bytes = s->peak_bytes;
     if (budget_bytes) *budget_bytes = s->budget_bytes;
     if (rounds) *rounds = s->rounds;
+    return LBM_OK;
+}
+
+int lbm_server_admission(lbm_server *s, int *peak_active, long long *memory_waits)
+{
+    if (!s) return LBM_EINVAL;
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (peak_active) *peak_active = s->peak_active;
+    if (memory_waits) *memory_waits = s->memory_waits;
+    return LBM_OK;
+}
+
+int lbm_server_times(lbm_server *s, long long id, double *queued_s, double *run_s)
+{
+    if (!s) return LBM_EINVAL;
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->all.find(id);
+    if (it == s->all.end()) return LBM_EINVAL;
+    const Request &r = *it->second;
+    if (r.state < 2) return LBM_ESTATE;
+    if (queued_s) *queued_s = std::chrono::duration<double>(r.t_start - r.t_submit).count();
+    if (run_s) *run_s = std::chrono::duration<double>(r.t_end - r.t_start).count();
     return LBM_OK;
 }
 

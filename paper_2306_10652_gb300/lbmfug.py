@@ -108,6 +108,8 @@ _sig("lbm_server_result", ctypes.c_int, _vp, ctypes.c_longlong, _dp)
 _sig("lbm_server_wait_all", ctypes.c_int, _vp)
 _sig("lbm_server_stats", ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
      ctypes.POINTER(ctypes.c_size_t), _dp, ctypes.POINTER(ctypes.c_longlong))
+_sig("lbm_server_admission", ctypes.c_int, _vp, _ip, ctypes.POINTER(ctypes.c_longlong))
+_sig("lbm_server_times", ctypes.c_int, _vp, ctypes.c_longlong, _dp, _dp)
 _sig("lbm_server_destroy", ctypes.c_int, _vp)
 _sig("lbm_synchronize", ctypes.c_int, _vp)
 _sig("lbm_destroy", ctypes.c_int, _vp)
@@ -121,7 +123,8 @@ EXPORTED = ["lbm_options_default", "lbm_create", "lbm_set_options", "lbm_init_fi
             "lbm_forces", "lbm_schedule_info", "lbm_field_sums_noalloc", "lbm_batch_create", "lbm_batch_run",
             "lbm_batch_job_state", "lbm_batch_info", "lbm_batch_set_threads", "lbm_batch_destroy",
             "lbm_server_estimate_bytes", "lbm_server_create", "lbm_server_submit", "lbm_server_poll",
-            "lbm_server_result", "lbm_server_wait_all", "lbm_server_stats", "lbm_server_destroy",
+            "lbm_server_result", "lbm_server_wait_all", "lbm_server_stats", "lbm_server_admission",
+            "lbm_server_times", "lbm_server_destroy",
             "lbm_synchronize", "lbm_destroy", "lbm_lattice_velocities", "lbm_strerror"]
 
 
@@ -503,6 +506,18 @@ class Server:
                                      ctypes.byref(bud), ctypes.byref(rd)), "lbm_server_stats")
         return {"submitted": sub.value, "completed": comp.value, "peak_bytes": peak.value,
                 "budget_bytes": bud.value, "rounds": rd.value}
+
+    def admission(self):
+        """{"peak_active", "memory_waits"} (lbm_server_admission)."""
+        pa, mw = ctypes.c_int(), ctypes.c_longlong()
+        _check(_lib.lbm_server_admission(self._h, ctypes.byref(pa), ctypes.byref(mw)), "lbm_server_admission")
+        return {"peak_active": pa.value, "memory_waits": mw.value}
+
+    def times(self, jid):
+        """(queued seconds, running seconds) of a finished request (lbm_server_times)."""
+        q, r = ctypes.c_double(), ctypes.c_double()
+        _check(_lib.lbm_server_times(self._h, int(jid), ctypes.byref(q), ctypes.byref(r)), "lbm_server_times")
+        return q.value, r.value
 
     def close(self):
         if self._h is not None:

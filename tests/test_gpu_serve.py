@@ -71,6 +71,12 @@ def test_admission_respects_budget():
         st = srv.stats()
         assert st["peak_bytes"] <= st["budget_bytes"] < 2 * need
         assert all(srv.poll(j)["state"] == "exhausted" for j in ids)
+        # one job at a time: the two later requests waited for memory with slots free
+        adm = srv.admission()
+        assert adm["peak_active"] == 1 and adm["memory_waits"] == 2, adm
+        times = [srv.times(j) for j in ids]
+        assert all(q >= 0.0 and r > 0.0 for q, r in times)
+        assert times[2][0] >= times[0][1]  # the third queued at least as long as the first ran
         # a request that can never fit is refused at submission
         lat, c, rho = reqs[0]
         big = np.ones((2, 1, 512, 1024)) * 0.1
@@ -98,3 +104,35 @@ def test_failed_job_is_retired_and_others_finish():
         pb = srv.poll(jb)
         assert pb["state"] == "failed" and pb["status"] != 0
         assert all(srv.poll(j)["state"] == "exhausted" for j in ids)
+
+
+@pytest.mark.parametrize("lat,shape,nc,precision", [
+    (0, (1, 512, 640), 10, FP32DEV), (0, (1, 256, 384), 4, 0), (1, (48, 56, 64), 7, FP32DEV),
+    (1, (32, 40, 48), 3, 0)])
+def test_estimate_covers_allocation(lat, shape, nc, precision):
+    """lbm_server_estimate_bytes is at least what a handle of that size
+    allocates on the device (measured as the drop of free device memory
+    across initialisation), and not far above it."""
+    import torch
+    lbmfug = lb()
+    c = seeded_mixture(140, nc, lat, shape)
+    rho = smooth_rho(140, c, shape, 0.02, 0.12)
+    est = lbmfug.lbm_server_estimate_bytes(lat, shape[2], shape[1], shape[0], nc, precision)
+    small = (1, 8, 16) if lat == 0 else (4, 5, 6)  # loads the kernels before the measurement
+    with gpu_problem(seeded_mixture(141, nc, lat, small), lat, small, precision=precision) as gp:
+        gp.init_fields(smooth_rho(141, seeded_mixture(141, nc, lat, small), small, 0.02, 0.12))
+        gp.step(2)
+        gp.convergence()
+        gp.synchronize()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    free0, _ = torch.cuda.mem_get_info()
+    with gpu_problem(c, lat, shape, precision=precision) as gp:
+        gp.init_fields(rho)
+        gp.step(2)
+        gp.convergence()  # allocates the convergence snapshot
+        gp.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+    used = free0 - free1
+    assert used <= est, (used, est)
+    assert est <= 1.3 * used + (64 << 20), (used, est)
