@@ -50,6 +50,20 @@ __device__ __forceinline__ F2 two_sum(float a, float b)
     return {s, e};
 }
 
+// TwoSum of two non-negative numbers: FastTwoSum of the larger and the
+// smaller, which is exact, so (s, e) equals two_sum's.  The operands are
+// ordered by their bit patterns, which order non-negative binary32 numbers as
+// their values and put a NaN above every number, so a NaN propagates.  Three
+// additions on the FMA pipe and two integer min/max on the ALU pipe, against
+// six additions.
+__device__ __forceinline__ F2 two_sum_pos(float a, float b)
+{
+    const int ia = __float_as_int(a), ib = __float_as_int(b);
+    const float big = __int_as_float(max(ia, ib)), small = __int_as_float(min(ia, ib));
+    const float s = __fadd_rn(big, small);
+    return {s, __fsub_rn(small, __fsub_rn(s, big))};
+}
+
 __device__ __forceinline__ F2 fast_two_sum(float a, float b)  // |a| >= |b|
 {
     const float s = __fadd_rn(a, b);
@@ -135,6 +149,34 @@ struct Dot {
     __device__ __forceinline__ void add_term(F2 t)
     {
         const F2 u = two_sum(s, t.hi);
+        s = u.hi;
+        c = __fadd_rn(c, __fadd_rn(u.lo, t.lo));
+    }
+    __device__ __forceinline__ F2 value() const { return fast_two_sum(s, c); }
+};
+
+// Dot for sums whose products c_j.hi x_j.hi are all non-negative (the
+// mixture sums of Eqs. 4, 10 and 11: positive parameters times positive
+// densities): the same operations as Dot with two_sum_pos for the running
+// sum, so the same result.
+struct DotPos {
+    float s, c;
+    __device__ __forceinline__ void first(F2 cj, F2 xj)
+    {
+        const F2 p = two_prod(cj.hi, xj.hi);
+        s = p.hi;
+        c = fmaf(cj.hi, xj.lo, fmaf(cj.lo, xj.hi, p.lo));
+    }
+    __device__ __forceinline__ void add(F2 cj, F2 xj)
+    {
+        const F2 p = two_prod(cj.hi, xj.hi);
+        const F2 t = two_sum_pos(s, p.hi);
+        s = t.hi;
+        c = __fadd_rn(c, __fadd_rn(t.lo, fmaf(cj.hi, xj.lo, fmaf(cj.lo, xj.hi, p.lo))));
+    }
+    __device__ __forceinline__ void add_term(F2 t)  // t.hi >= 0
+    {
+        const F2 u = two_sum_pos(s, t.hi);
         s = u.hi;
         c = __fadd_rn(c, __fadd_rn(u.lo, t.lo));
     }

@@ -61,10 +61,14 @@ struct Dot2x {
         const float2 ch = make_float2(A.x, A.y), cl = make_float2(A.z, A.w);
         const float2 p = __fmul2_rn(ch, X);
         const float2 pe = __ffma2_rn(ch, X, pneg(p));
-        // TwoSum(s, p) lane by lane
-        const float2 t = __fadd2_rn(s, p);
-        const float2 bp = __fadd2_rn(t, pneg(s));
-        const float2 e = __fadd2_rn(__fadd2_rn(s, pneg(__fadd2_rn(t, pneg(bp)))), __fadd2_rn(p, pneg(bp)));
+        // TwoSum(s, p) lane by lane, as FastTwoSum of the larger and the
+        // smaller (both non-negative: see two_sum_pos)
+        const int sx = __float_as_int(s.x), sy = __float_as_int(s.y);
+        const int px = __float_as_int(p.x), py = __float_as_int(p.y);
+        const float2 big = make_float2(__int_as_float(max(sx, px)), __int_as_float(max(sy, py)));
+        const float2 small = make_float2(__int_as_float(min(sx, px)), __int_as_float(min(sy, py)));
+        const float2 t = __fadd2_rn(big, small);
+        const float2 e = __fadd2_rn(small, pneg(__fadd2_rn(t, pneg(big))));
         s = t;
         c = __fadd2_rn(c, __fadd2_rn(e, __ffma2_rn(ch, XL, __ffma2_rn(cl, X, pe))));
     }
@@ -74,7 +78,7 @@ struct Dot2x {
 template <int NC>
 __device__ __forceinline__ F2 psi(const Params &P, const float (&h)[NC], const float (&l)[NC])
 {
-    Dot d;
+    DotPos d;
     d.first(f2(P.dPk[0]), {h[0], l[0]});
 #pragma unroll
     for (int j = 1; j < NC; ++j) d.add(f2(P.dPk[j]), {h[j], l[j]});
@@ -108,7 +112,7 @@ __device__ __forceinline__ void mu(const Params &P, const float4 *__restrict__ t
     constexpr double kS2 = 1.41421356237309504880168872421;
     // rho~_i and rho~ = sum_i rho~_i
     F2 y[NC];
-    Dot rt;
+    DotPos rt;
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
         y[i] = Dot::term(f2(P.dM[i]), {h[i], l[i]});
@@ -121,7 +125,7 @@ __device__ __forceinline__ void mu(const Params &P, const float4 *__restrict__ t
     }
     const F2 rho = rt.value();
     // Eq. (11) times rho~: B = b_m rho~
-    Dot bd;
+    DotPos bd;
     bd.first(f2(P.dB[0]), {h[0], l[0]});
 #pragma unroll
     for (int j = 1; j < NC; ++j) bd.add(f2(P.dB[j]), {h[j], l[j]});
@@ -138,13 +142,13 @@ __device__ __forceinline__ void mu(const Params &P, const float4 *__restrict__ t
         T[2 * r + 1] = fast_two_sum(t.s.y, t.c.y);
     }
     if constexpr (NC % 2 == 1) {
-        Dot t;
+        DotPos t;
         t.first(f2(P.dA[(NC - 1) * kMaxNc]), {h[0], l[0]});
 #pragma unroll
         for (int j = 1; j < NC; ++j) t.add(f2(P.dA[(NC - 1) * kMaxNc + j]), {h[j], l[j]});
         T[NC - 1] = t.value();
     }
-    Dot qd;
+    DotPos qd;
     qd.first(y[0], T[0]);
 #pragma unroll
     for (int i = 1; i < NC; ++i) qd.add(y[i], T[i]);
@@ -193,7 +197,7 @@ __device__ __forceinline__ void mu_rolled(const Params &P, const float4 *__restr
 {
     constexpr double kS2 = 1.41421356237309504880168872421;
     F2 y[NC];
-    Dot rt;
+    DotPos rt;
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
         PH[i * pitch] = h[i];
@@ -207,7 +211,7 @@ __device__ __forceinline__ void mu_rolled(const Params &P, const float4 *__restr
         }
     }
     const F2 rho = rt.value();
-    Dot bd;
+    DotPos bd;
     bd.first(f2(P.dB[0]), {h[0], l[0]});
 #pragma unroll
     for (int j = 1; j < NC; ++j) bd.add(f2(P.dB[j]), {h[j], l[j]});
@@ -223,14 +227,14 @@ __device__ __forceinline__ void mu_rolled(const Params &P, const float4 *__restr
         TS[(2 * r + 1) * pitch] = make_float2(b.hi, b.lo);
     }
     if constexpr (NC % 2 == 1) {
-        Dot t;
+        DotPos t;
         t.first(f2(P.dA[(NC - 1) * kMaxNc]), {h[0], l[0]});
 #pragma unroll
         for (int j = 1; j < NC; ++j) t.add(f2(P.dA[(NC - 1) * kMaxNc + j]), {h[j], l[j]});
         const F2 v = t.value();
         TS[(NC - 1) * pitch] = make_float2(v.hi, v.lo);
     }
-    Dot qd;
+    DotPos qd;
     qd.first(y[0], f2(TS[0]));
 #pragma unroll
     for (int i = 1; i < NC; ++i) qd.add(y[i], f2(TS[i * pitch]));
