@@ -370,17 +370,17 @@ constexpr int kWmax32 = kT - 6;  // binary32 kernel: one density column per thre
 //     difference mu(r + e) - mu(r - e) taken on the (hi, lo) pairs and
 //     rounded once (so it carries the df64 accuracy of mu), written to
 //     G[i][node] = (d mu_i / dx, d mu_i / dy) in binary32.
-// The step kernel forms F_i = -rho~_i G_i.  psi rows live in a ring of four
-// and mu rows in a ring of three: a slot is rewritten only after the barrier
-// that follows its last reader.
+// The step kernel forms F_i = -rho~_i G_i.  psi and mu rows live in rings of
+// three: a slot is rewritten only after the barrier that follows its last
+// reader.  The log table is read from device memory (through L1), so that
+// five CTAs fit on an SM.
 constexpr int kWmaxMu = kT - 4;
 
 template <int NC> struct SmemMu {
     static __host__ __device__ constexpr size_t bytes()
     {
-        // log table, psi ring, mu ring, per-thread scratch of mu_rolled (PH, PL, TS)
-        return (size_t)df::kLogTab * sizeof(float4) + 4 * kT * sizeof(float2) + 3 * NC * kT * sizeof(float2) +
-               (size_t)NC * kT * (2 * sizeof(float) + sizeof(float2));
+        // psi ring, mu ring, per-thread scratch of mu_rolled (T_i)
+        return 3 * kT * sizeof(float2) + 3 * NC * kT * sizeof(float2) + (size_t)NC * kT * sizeof(float2);
     }
 };
 
@@ -389,12 +389,10 @@ __global__ void __launch_bounds__(kT) k_mu32(const Params P, const int W, const 
                                              float2 *__restrict__ G)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    float4 *LT = (float4 *)smem;                                           // [128]
-    float2 *PS = (float2 *)(smem + df::kLogTab * sizeof(float4));          // [4][kT]
-    float2 *MU = PS + 4 * kT;                                              // [3][NC][kT]
-    float2 *TS = MU + 3 * NC * kT;                                         // [NC][kT] T_i
-    float *PHs = (float *)(TS + NC * kT);                                  // [NC][kT] pair hi
-    float *PLs = PHs + NC * kT;                                            // [NC][kT] pair lo
+    float2 *PS = (float2 *)smem;   // [3][kT]
+    float2 *MU = PS + 3 * kT;      // [3][NC][kT]
+    float2 *TS = MU + 3 * NC * kT; // [NC][kT] T_i
+    const float4 *LT = P.dlogtab;  // [128], device memory
     const int nx = P.nx, ny = P.ny;
     const IDX N = (IDX)P.N;
     const int x0 = blockIdx.x * W;
@@ -409,31 +407,31 @@ __global__ void __launch_bounds__(kT) k_mu32(const Params P, const int W, const 
     const int xg = wrapc(x0 + c, nx);
     const float *rhin = in.rhi_f();
     const float *rlin = in.rlo;
-    for (int j = t; j < df::kLogTab; j += kT) LT[j] = P.logtab[j];
     float ph[NC], pl[NC];  // density pairs of row k-1 at this column
+    IDX rbp = 0;           // their node index
 #pragma unroll
     for (int i = 0; i < NC; ++i) ph[i] = pl[i] = 0.0f;
     for (int kk = 0; kk < h + 4; ++kk) {
         const int k = y0 - 2 + kk;
         float hh[NC], ll[NC];
+        const IDX rb = (IDX)wrapc(k, ny) * (IDX)nx + (IDX)xg;
         if (hasP) {
-            const IDX rb = (IDX)wrapc(k, ny) * (IDX)nx + (IDX)xg;
 #pragma unroll
             for (int i = 0; i < NC; ++i) {
                 hh[i] = __ldg(rhin + i * N + rb);
                 ll[i] = __ldg(rlin + i * N + rb);
             }
             const df::F2 ps = df::psi<NC>(P, hh, ll);
-            PS[(kk & 3) * kT + t] = make_float2(ps.hi, ps.lo);
+            PS[(kk % 3) * kT + t] = make_float2(ps.hi, ps.lo);
         }
         __syncthreads();
         if (kk >= 2 && kk < h + 4 && hasM) {
-            const float2 *p0 = PS + ((kk - 2) & 3) * kT, *p1 = PS + ((kk - 1) & 3) * kT, *p2 = PS + (kk & 3) * kT;
+            const float2 *p0 = PS + ((kk - 2) % 3) * kT, *p1 = PS + ((kk - 1) % 3) * kT, *p2 = PS + (kk % 3) * kT;
             const df::F2 lap = df::lap9(df::f2(p1[t]), df::f2(p1[t + 1]), df::f2(p1[t - 1]), df::f2(p2[t]),
                                         df::f2(p0[t]), df::f2(p2[t + 1]), df::f2(p2[t - 1]), df::f2(p0[t + 1]),
                                         df::f2(p0[t - 1]));
-            df::mu_rolled<NC>(P, LT, ph, pl, lap, PHs + t, PLs + t, TS + t, kT,
-                              MU + ((kk - 1) % 3) * NC * kT + t, kT);
+            df::mu_rolled<NC, IDX>(P, LT, ph, pl, lap, rhin + rbp, rlin + rbp, N, TS + t, kT,
+                                   MU + ((kk - 1) % 3) * NC * kT + t, kT);
         }
         if (hasP) {
 #pragma unroll
@@ -441,6 +439,7 @@ __global__ void __launch_bounds__(kT) k_mu32(const Params P, const int W, const 
                 ph[i] = hh[i];
                 pl[i] = ll[i];
             }
+            rbp = rb;
         }
         __syncthreads();
         if (kk >= 4 && interior) {

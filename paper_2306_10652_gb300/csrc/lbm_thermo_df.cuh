@@ -89,7 +89,9 @@ __device__ __forceinline__ F2 psi(const Params &P, const float (&h)[NC], const f
 //            = (4 (faces) + (diagonals) - 20 X(r)) / 6
 __device__ __forceinline__ F2 lap9(F2 c, F2 e, F2 w, F2 n, F2 s, F2 ne, F2 nw, F2 se, F2 sw)
 {
-    Dot a;
+    // the neighbours' psi are non-negative (Eq. 4): their running sum takes
+    // two_sum_pos; the centre term, negative, the general TwoSum
+    DotPos a;
     a.s = __fmul_rn(4.0f, e.hi);
     a.c = __fmul_rn(4.0f, e.lo);
     a.add_term({__fmul_rn(4.0f, w.hi), __fmul_rn(4.0f, w.lo)});
@@ -99,9 +101,12 @@ __device__ __forceinline__ F2 lap9(F2 c, F2 e, F2 w, F2 n, F2 s, F2 ne, F2 nw, F
     a.add_term(nw);
     a.add_term(se);
     a.add_term(sw);
+    Dot b;
+    b.s = a.s;
+    b.c = a.c;
     const F2 c20 = two_prod(-20.0f, c.hi);
-    a.add_term({c20.hi, fmaf(-20.0f, c.lo, c20.lo)});
-    return mul(a.value(), {hi_of(1.0 / 6.0), lo_of(1.0 / 6.0)});
+    b.add_term({c20.hi, fmaf(-20.0f, c.lo, c20.lo)});
+    return mul(b.value(), {hi_of(1.0 / 6.0), lo_of(1.0 / 6.0)});
 }
 
 // mu_i = RT ln f_i - sqrt(kappa_i) lap psi for i < NC at one node
@@ -187,12 +192,14 @@ __device__ __forceinline__ void mu(const Params &P, const float4 *__restrict__ t
 // components (the unrolled form above is a few thousand instructions of
 // straight-line code at Nc = 10, more than the instruction cache holds).
 // The same operations in the same order, so the result is bitwise that of
-// mu().  Per-thread scratch in shared memory with stride `pitch` floats:
-// PH, PL [NC] (the density pair), TS [NC] float2 (T_i); mu_i is written to
-// out[i * ostride].
-template <int NC>
+// mu().  The component loop re-reads the density pair of component i from
+// the state, gh[i * gstride] and gl[i * gstride] (the values in h, l), one
+// component ahead; T_i goes through per-thread shared-memory scratch TS [NC]
+// float2 with stride `pitch`; mu_i is written to out[i * ostride].
+template <int NC, typename IDX>
 __device__ __forceinline__ void mu_rolled(const Params &P, const float4 *__restrict__ tab, const float (&h)[NC],
-                                          const float (&l)[NC], F2 lap, float *PH, float *PL, float2 *TS, int pitch,
+                                          const float (&l)[NC], F2 lap, const float *__restrict__ gh,
+                                          const float *__restrict__ gl, IDX gstride, float2 *TS, int pitch,
                                           float2 *out, int ostride)
 {
     constexpr double kS2 = 1.41421356237309504880168872421;
@@ -200,8 +207,6 @@ __device__ __forceinline__ void mu_rolled(const Params &P, const float4 *__restr
     DotPos rt;
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
-        PH[i * pitch] = h[i];
-        PL[i * pitch] = l[i];
         y[i] = Dot::term(f2(P.dM[i]), {h[i], l[i]});
         if (i == 0) {
             rt.s = y[0].hi;
@@ -253,10 +258,16 @@ __device__ __forceinline__ void mu_rolled(const Params &P, const float4 *__restr
                        mul(mul(Q, u), add(mul(Lu, {hi_of(0.5 / kS2), lo_of(0.5 / kS2)}), neg(w))));
     const F2 RC2 = mul(Lu, {hi_of(-1.0 / kS2), lo_of(-1.0 / kS2)});
     const F2 RG = mul(RT, lnomB);
+    float hn = __ldg(gh), ln = __ldg(gl);
 #pragma unroll 1
     for (int i = 0; i < NC; ++i) {
+        const float hc = hn, lc = ln;
+        if (i + 1 < NC) {
+            hn = __ldg(gh + (IDX)(i + 1) * gstride);
+            ln = __ldg(gl + (IDX)(i + 1) * gstride);
+        }
         Dot a;
-        const F2 t0 = mul_u(RT, log({PH[i * pitch], PL[i * pitch]}, tab));
+        const F2 t0 = mul_u(RT, log({hc, lc}, tab));
         a.s = t0.hi;
         a.c = t0.lo;
         a.add_term(f2(P.dRK[i]));
