@@ -370,13 +370,6 @@ int ensure_allocated(lbm_problem *p)
         p->psi2 = (float2 *)dev_alloc(p, (size_t)p->N * sizeof(float2));
         if (!p->mu || !p->psi2) return LBM_ENOMEM;
     }
-    {
-        float4 *tab = (float4 *)dev_alloc(p, sizeof(p->P.logtab));
-        if (!tab) return LBM_ENOMEM;
-        if (cudaMemcpyAsync(tab, p->P.logtab, sizeof(p->P.logtab), cudaMemcpyHostToDevice, p->stream) != cudaSuccess)
-            return LBM_ECUDA;
-        p->P.dlogtab = tab;
-    }
     if (cudaMemsetAsync(p->flag, 0, 16, p->stream) != cudaSuccess) return LBM_ECUDA;
     p->allocated = true;
     return LBM_OK;

@@ -84,7 +84,6 @@ struct Params {
     float2 dPk[kMaxNc];          // sqrt(kappa_j) / M_j
     float2 dRT;                  // RT
     float4 logtab[128];          // df64 logarithm table (lbm_df64.cuh)
-    const float4 *dlogtab;       // the same table in device memory (read through L1 by the mu pass)
 };
 
 // Parameter access in the arithmetic type E of a kernel.

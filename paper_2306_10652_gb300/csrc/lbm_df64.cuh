@@ -188,15 +188,36 @@ constexpr int kLogTab = 128;
 
 constexpr double kLn2 = 0.693147180559945309417232121458;
 
+// Views of the table: its float4 entries, or the same values split into
+// {v_j, -ln v_j hi} pairs and the lo words (1.5 KB of shared memory, not 2).
+struct TabF4 {
+    const float4 *__restrict__ p;
+    __device__ __forceinline__ float3 operator[](int j) const
+    {
+        const float4 t = p[j];
+        return make_float3(t.x, t.y, t.z);
+    }
+};
+struct TabSplit {
+    const float2 *__restrict__ vt;
+    const float *__restrict__ tl;
+    __device__ __forceinline__ float3 operator[](int j) const
+    {
+        const float2 a = vt[j];
+        return make_float3(a.x, a.y, tl[j]);
+    }
+};
+
 // ln(x.hi + x.lo) for x.hi a positive normal binary32 number (NaN otherwise),
 // unnormalised result.  ln(hi + lo) = ln hi + lo/hi to 2^-49.
-__device__ __forceinline__ F2 log(F2 x, const float4 *__restrict__ tab)
+template <typename Tab>
+__device__ __forceinline__ F2 log(F2 x, Tab tab)
 {
     const int u = __float_as_int(x.hi);
     const int ex = u >> 23;  // biased exponent (x > 0)
     const float kf = __fsub_rn(__int_as_float(0x4b000000 + ex), 8388608.0f + 127.0f);
     const float m = __int_as_float((u & 0x007fffff) | 0x3f800000);
-    const float4 t = tab[(u >> 16) & 0x7f];
+    const float3 t = tab[(u >> 16) & 0x7f];
     const F2 P = two_prod(m, t.x);
     const float r = __fsub_rn(P.hi, 1.0f);  // exact
     // first-order terms of the two small remainders: P.lo / P.hi and x.lo / x.hi
@@ -214,6 +235,8 @@ __device__ __forceinline__ F2 log(F2 x, const float4 *__restrict__ tab)
     const bool ok = x.hi >= 1.17549435e-38f && x.hi <= 3.40282347e38f;
     return {ok ? s.hi : __int_as_float(0x7fc00000), lo};
 }
+
+__device__ __forceinline__ F2 log(F2 x, const float4 *__restrict__ tab) { return log(x, TabF4{tab}); }
 
 // Host: fill the log table (binary64 arithmetic; called once per problem).
 inline void make_log_table(float *tab4)

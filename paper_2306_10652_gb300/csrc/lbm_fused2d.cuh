@@ -372,15 +372,18 @@ constexpr int kWmax32 = kT - 6;  // binary32 kernel: one density column per thre
 //     G[i][node] = (d mu_i / dx, d mu_i / dy) in binary32.
 // The step kernel forms F_i = -rho~_i G_i.  psi and mu rows live in rings of
 // three: a slot is rewritten only after the barrier that follows its last
-// reader.  The log table is read from device memory (through L1), so that
-// five CTAs fit on an SM.
+// reader.  mu_rolled keeps T_i in the thread's own mu slots of the row it is
+// writing (it reads T_i just before it writes mu_i there), and the log table
+// is split into {v, -ln v hi} pairs and lo words, so that a CTA needs 44.5 KB
+// of shared memory at Nc = 10 and five fit on an SM.
 constexpr int kWmaxMu = kT - 4;
 
 template <int NC> struct SmemMu {
     static __host__ __device__ constexpr size_t bytes()
     {
-        // psi ring, mu ring, per-thread scratch of mu_rolled (T_i)
-        return 3 * kT * sizeof(float2) + 3 * NC * kT * sizeof(float2) + (size_t)NC * kT * sizeof(float2);
+        // log table (pairs, lo words), psi ring, mu ring, density-pair scratch of mu_rolled
+        return (size_t)df::kLogTab * (sizeof(float2) + sizeof(float)) + 3 * kT * sizeof(float2) +
+               3 * NC * kT * sizeof(float2) + 2 * (size_t)NC * kT * sizeof(float);
     }
 };
 
@@ -389,10 +392,12 @@ __global__ void __launch_bounds__(kT) k_mu32(const Params P, const int W, const 
                                              float2 *__restrict__ G)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    float2 *PS = (float2 *)smem;   // [3][kT]
-    float2 *MU = PS + 3 * kT;      // [3][NC][kT]
-    float2 *TS = MU + 3 * NC * kT; // [NC][kT] T_i
-    const float4 *LT = P.dlogtab;  // [128], device memory
+    float2 *LV = (float2 *)smem;          // [128] {v_j, -ln v_j hi}
+    float *LL = (float *)(LV + df::kLogTab);  // [128] -ln v_j lo
+    float2 *PS = (float2 *)(LL + df::kLogTab);  // [3][kT]
+    float2 *MU = PS + 3 * kT;             // [3][NC][kT]
+    float *PHs = (float *)(MU + 3 * NC * kT);  // [NC][kT] pair hi
+    float *PLs = PHs + NC * kT;           // [NC][kT] pair lo
     const int nx = P.nx, ny = P.ny;
     const IDX N = (IDX)P.N;
     const int x0 = blockIdx.x * W;
@@ -407,15 +412,19 @@ __global__ void __launch_bounds__(kT) k_mu32(const Params P, const int W, const 
     const int xg = wrapc(x0 + c, nx);
     const float *rhin = in.rhi_f();
     const float *rlin = in.rlo;
+    for (int j = t; j < df::kLogTab; j += kT) {
+        LV[j] = make_float2(P.logtab[j].x, P.logtab[j].y);
+        LL[j] = P.logtab[j].z;
+    }
+    const df::TabSplit LT{LV, LL};
     float ph[NC], pl[NC];  // density pairs of row k-1 at this column
-    IDX rbp = 0;           // their node index
 #pragma unroll
     for (int i = 0; i < NC; ++i) ph[i] = pl[i] = 0.0f;
     for (int kk = 0; kk < h + 4; ++kk) {
         const int k = y0 - 2 + kk;
         float hh[NC], ll[NC];
-        const IDX rb = (IDX)wrapc(k, ny) * (IDX)nx + (IDX)xg;
         if (hasP) {
+            const IDX rb = (IDX)wrapc(k, ny) * (IDX)nx + (IDX)xg;
 #pragma unroll
             for (int i = 0; i < NC; ++i) {
                 hh[i] = __ldg(rhin + i * N + rb);
@@ -430,8 +439,8 @@ __global__ void __launch_bounds__(kT) k_mu32(const Params P, const int W, const 
             const df::F2 lap = df::lap9(df::f2(p1[t]), df::f2(p1[t + 1]), df::f2(p1[t - 1]), df::f2(p2[t]),
                                         df::f2(p0[t]), df::f2(p2[t + 1]), df::f2(p2[t - 1]), df::f2(p0[t + 1]),
                                         df::f2(p0[t - 1]));
-            df::mu_rolled<NC, IDX>(P, LT, ph, pl, lap, rhin + rbp, rlin + rbp, N, TS + t, kT,
-                                   MU + ((kk - 1) % 3) * NC * kT + t, kT);
+            float2 *out = MU + ((kk - 1) % 3) * NC * kT + t;
+            df::mu_rolled<NC>(P, LT, ph, pl, lap, PHs + t, PLs + t, out, kT, out, kT);
         }
         if (hasP) {
 #pragma unroll
@@ -439,7 +448,6 @@ __global__ void __launch_bounds__(kT) k_mu32(const Params P, const int W, const 
                 ph[i] = hh[i];
                 pl[i] = ll[i];
             }
-            rbp = rb;
         }
         __syncthreads();
         if (kk >= 4 && interior) {

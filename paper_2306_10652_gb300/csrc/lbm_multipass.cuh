@@ -83,8 +83,8 @@ __global__ void __launch_bounds__(kThreads) k_mp_psi(const Params P, StateBufs s
     }
 }
 
-// per-thread scratch of mu_rolled: TS [NC] float2
-template <int NC> constexpr size_t mp_mu_smem() { return (size_t)NC * kThreads * sizeof(float2); }
+// per-thread scratch of mu_rolled: PH, PL [NC] floats and TS [NC] float2
+template <int NC> constexpr size_t mp_mu_smem() { return (size_t)NC * kThreads * (2 * sizeof(float) + sizeof(float2)); }
 
 template <int LAT, int NC>
 __global__ void __launch_bounds__(kThreads)
@@ -94,6 +94,8 @@ __global__ void __launch_bounds__(kThreads)
     __shared__ float4 LT[df::kLogTab];
     extern __shared__ __align__(16) unsigned char scratch[];
     float2 *TS = (float2 *)scratch;
+    float *PH = (float *)(TS + NC * kThreads);
+    float *PL = PH + NC * kThreads;
     const int t = threadIdx.x;
     for (int j = t; j < df::kLogTab; j += blockDim.x) LT[j] = P.logtab[j];
     __syncthreads();
@@ -107,8 +109,7 @@ __global__ void __launch_bounds__(kThreads)
             h[i] = __ldg(st.rhi_f() + (long long)i * N + r);
             l[i] = __ldg(st.rlo + (long long)i * N + r);
         }
-        df::mu_rolled<NC, int>(P, LT, h, l, lapQ<LAT>(psi, nb), st.rhi_f() + r, st.rlo + r, N, TS + t, kThreads,
-                               mu + r, N);
+        df::mu_rolled<NC>(P, df::TabF4{LT}, h, l, lapQ<LAT>(psi, nb), PH + t, PL + t, TS + t, kThreads, mu + r, N);
     }
 }
 

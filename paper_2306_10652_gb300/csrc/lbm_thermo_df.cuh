@@ -192,21 +192,22 @@ __device__ __forceinline__ void mu(const Params &P, const float4 *__restrict__ t
 // components (the unrolled form above is a few thousand instructions of
 // straight-line code at Nc = 10, more than the instruction cache holds).
 // The same operations in the same order, so the result is bitwise that of
-// mu().  The component loop re-reads the density pair of component i from
-// the state, gh[i * gstride] and gl[i * gstride] (the values in h, l), one
-// component ahead; T_i goes through per-thread shared-memory scratch TS [NC]
-// float2 with stride `pitch`; mu_i is written to out[i * ostride].
-template <int NC, typename IDX>
-__device__ __forceinline__ void mu_rolled(const Params &P, const float4 *__restrict__ tab, const float (&h)[NC],
-                                          const float (&l)[NC], F2 lap, const float *__restrict__ gh,
-                                          const float *__restrict__ gl, IDX gstride, float2 *TS, int pitch,
-                                          float2 *out, int ostride)
+// mu().  Per-thread scratch in shared memory with stride `pitch`: PH, PL [NC]
+// floats (the density pair) and TS [NC] float2 (T_i); mu_i is written to
+// out[i * ostride].  TS may be out itself (same stride): iteration i reads
+// T_i before it stores mu_i.  Tab: a view of the log table (lbm_df64.cuh).
+template <int NC, typename Tab>
+__device__ __forceinline__ void mu_rolled(const Params &P, Tab tab, const float (&h)[NC], const float (&l)[NC],
+                                          F2 lap, float *PH, float *PL, float2 *TS, int pitch, float2 *out,
+                                          int ostride)
 {
     constexpr double kS2 = 1.41421356237309504880168872421;
     F2 y[NC];
     DotPos rt;
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
+        PH[i * pitch] = h[i];
+        PL[i * pitch] = l[i];
         y[i] = Dot::term(f2(P.dM[i]), {h[i], l[i]});
         if (i == 0) {
             rt.s = y[0].hi;
@@ -258,16 +259,10 @@ __device__ __forceinline__ void mu_rolled(const Params &P, const float4 *__restr
                        mul(mul(Q, u), add(mul(Lu, {hi_of(0.5 / kS2), lo_of(0.5 / kS2)}), neg(w))));
     const F2 RC2 = mul(Lu, {hi_of(-1.0 / kS2), lo_of(-1.0 / kS2)});
     const F2 RG = mul(RT, lnomB);
-    float hn = __ldg(gh), ln = __ldg(gl);
 #pragma unroll 1
     for (int i = 0; i < NC; ++i) {
-        const float hc = hn, lc = ln;
-        if (i + 1 < NC) {
-            hn = __ldg(gh + (IDX)(i + 1) * gstride);
-            ln = __ldg(gl + (IDX)(i + 1) * gstride);
-        }
         Dot a;
-        const F2 t0 = mul_u(RT, log({hc, lc}, tab));
+        const F2 t0 = mul_u(RT, log({PH[i * pitch], PL[i * pitch]}, tab));
         a.s = t0.hi;
         a.c = t0.lo;
         a.add_term(f2(P.dRK[i]));
