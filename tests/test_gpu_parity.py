@@ -296,11 +296,14 @@ def test_fused_matches_threepass_many_shapes():
         assert np.abs(out[0] - out[1]).max() <= 1e-12 * scale, shape
 
 
-@pytest.mark.parametrize("lattice,shape,nc,steps", [(1, (6, 7, 9), 3, 5), (1, (5, 4, 6), 10, 3), (0, (1, 33, 70), 4, 5)])
+@pytest.mark.parametrize("lattice,shape,nc,steps", [(1, (6, 7, 9), 3, 5), (1, (5, 4, 6), 10, 3), (0, (1, 33, 70), 4, 5),
+                                                   (1, (5, 9, 70), 4, 3), (1, (3, 5, 33), 7, 2)])
 def test_multipass_several_steps(lattice, shape, nc, steps):
     """The multi-pass schedule (density update and psi of the next step in one
     pass) against the oracle over several steps: within 2e-6 of max |g_i|
-    per step (a few binary32 roundings per step on each population)."""
+    per step (a few binary32 roundings per step on each population).  The
+    shapes cover collide blocks (32 x 4 x 2 nodes in 3D, 32 x 8 in 2D) that
+    are ragged in every direction and boxes smaller than one block."""
     err = one_step_case(300 + nc, nc, lattice, shape, precision=FP32DEV, schedule=MULTIPASS, nsteps=steps)
     assert err < 2e-6 * steps, err
 
