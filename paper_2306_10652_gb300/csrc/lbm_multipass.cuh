@@ -133,8 +133,8 @@ template <int LAT, int NC> constexpr size_t mp_collide_smem()
 
 __device__ __forceinline__ int wrap_any(int v, int n)
 {
-    v %= n;
-    return v < 0 ? v + n : v;
+    if (v < 0) return v + n;  // v >= -1
+    return v < n ? v : v % n;
 }
 
 template <int LAT, int NC>
@@ -178,6 +178,14 @@ __global__ void __launch_bounds__(kThreads)
             const int gz = TL::HZ > 1 ? wrap_any(z0 + hz - 1, nz) : z0;
             return gx + nx * (gy + ny * gz);
         };
+        // the node of each tile entry this thread loads, once per block
+        constexpr int KPT = (TL::HN + kThreads - 1) / kThreads;
+        int gk[KPT];
+#pragma unroll
+        for (int q = 0; q < KPT; ++q) {
+            const int k = t + q * kThreads;
+            gk[q] = k < TL::HN ? gnode(k) : 0;
+        }
         int nb[Q];
         neighbours<LAT>(P, r, nb);
         // momentum sum_i sum_a e_a g_a and the total density
@@ -204,7 +212,9 @@ __global__ void __launch_bounds__(kThreads)
         for (int i = 0; i < NC; ++i) {
             __syncthreads();  // the previous tile's readers are done
             const float2 *mi = mu + (long long)i * N;
-            for (int k = t; k < TL::HN; k += kThreads) MT[k] = __ldg(mi + gnode(k));
+#pragma unroll
+            for (int q = 0; q < KPT; ++q)
+                if (t + q * kThreads < TL::HN) MT[t + q * kThreads] = __ldg(mi + gk[q]);
             __syncthreads();
             if (active) {
                 float g[3] = {0.0f, 0.0f, 0.0f};
@@ -234,10 +244,9 @@ __global__ void __launch_bounds__(kThreads)
         for (int i = 0; i < NC; ++i) {
             __syncthreads();
             const float *rhi = rh + (long long)i * N, *rli = rl + (long long)i * N;
-            for (int k = t; k < TL::HN; k += kThreads) {
-                const int g = gnode(k);
-                RT[k] = __ldg(rhi + g) + __ldg(rli + g);
-            }
+#pragma unroll
+            for (int q = 0; q < KPT; ++q)
+                if (t + q * kThreads < TL::HN) RT[t + q * kThreads] = __ldg(rhi + gk[q]) + __ldg(rli + gk[q]);
             __syncthreads();
             if (!active) continue;
             // grad rho_i from the neighbours' pairs (binary32)
