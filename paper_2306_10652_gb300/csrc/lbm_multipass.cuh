@@ -116,9 +116,10 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // A CTA of k_mp_collide owns a block of TX x TY x TZ nodes (one per thread)
-// and stages, component by component, the neighbours' mu_i and rho_i of the
-// block and its one-node halo in shared memory, so each value is read from
-// L2 about once instead of once per neighbour.
+// and stages the mu_i of every component for the block and its one-node halo
+// in shared memory (asynchronous copies, all in flight at once), then the
+// density pairs in the same space, so each neighbour value is read from L2
+// about once instead of once per neighbour.
 template <int LAT> struct MpTile {
     static constexpr int TX = 32, TY = LAT == 0 ? 8 : 4, TZ = LAT == 0 ? 1 : 2;
     static constexpr int HX = TX + 2, HY = TY + 2, HZ = LAT == 0 ? 1 : TZ + 2;
@@ -128,7 +129,24 @@ template <int LAT> struct MpTile {
 
 template <int LAT, int NC> constexpr size_t mp_collide_smem()
 {
-    return (size_t)NC * 3 * kThreads * sizeof(float) + MpTile<LAT>::HN * (sizeof(float2) + sizeof(float));
+    // forces, then one space for mu [NC][HN] (float2) or the pairs [2][NC][HN] (float)
+    return (size_t)NC * 3 * kThreads * sizeof(float) + (size_t)NC * MpTile<LAT>::HN * sizeof(float2);
+}
+
+// cp.async of 4 or 8 bytes from global to shared memory (both aligned to the size)
+__device__ __forceinline__ void cp_async4(void *sdst, const void *gsrc)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(a), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *sdst, const void *gsrc)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(a), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
 __device__ __forceinline__ int wrap_any(int v, int n)
@@ -147,8 +165,9 @@ __global__ void __launch_bounds__(kThreads)
     constexpr int D = L::D, Q = L::Q, NS = Q - 1;
     extern __shared__ __align__(16) unsigned char smem[];
     float *FS = (float *)smem;                        // [NC * 3][kThreads] this thread's forces F_i
-    float2 *MT = (float2 *)(FS + NC * 3 * kThreads);  // [HN] mu_i of the block and halo
-    float *RT = (float *)(MT + TL::HN);               // [HN] rho_i = hi + lo of the block and halo
+    float2 *MT = (float2 *)(FS + NC * 3 * kThreads);  // [NC][HN] mu_i of the block and halo
+    float *RH = (float *)MT;                          // [NC][HN] rho_i hi (after the forces)
+    float *RL = RH + NC * TL::HN;                     // [NC][HN] rho_i lo
     const float *gin = (const float *)in.g;
     float *gout = (float *)out.g;
     const float *rh = in.rhi_f();
@@ -208,19 +227,22 @@ __global__ void __launch_bounds__(kThreads)
         // Eq. (5): F_i = -rho~_i grad mu_i; grad X = 3 sum_pairs w e (X(r+e) - X(r-e)),
         // each difference on the (hi, lo) pairs rounded once
         float Fs[3] = {0.0f, 0.0f, 0.0f};
+        __syncthreads();  // the previous block's readers of the tiles are done
 #pragma unroll 1
-        for (int i = 0; i < NC; ++i) {
-            __syncthreads();  // the previous tile's readers are done
-            const float2 *mi = mu + (long long)i * N;
+        for (int i = 0; i < NC; ++i)
 #pragma unroll
             for (int q = 0; q < KPT; ++q)
-                if (t + q * kThreads < TL::HN) MT[t + q * kThreads] = __ldg(mi + gk[q]);
-            __syncthreads();
-            if (active) {
+                if (t + q * kThreads < TL::HN) cp_async8(MT + i * TL::HN + t + q * kThreads, mu + (long long)i * N + gk[q]);
+        cp_async_wait_all();
+        __syncthreads();
+        if (active) {
+#pragma unroll 1
+            for (int i = 0; i < NC; ++i) {
+                const float2 *mt = MT + i * TL::HN;
                 float g[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
                 for (int a = 1; a < Q; a += 2) {  // (a, a+1) opposite
-                    const float2 p = MT[ti + toff[a]], m = MT[ti + toff[a + 1]];
+                    const float2 p = mt[ti + toff[a]], m = mt[ti + toff[a + 1]];
                     const float dd = 3.0f * (float)L::w(a) * ((p.x - m.x) + (p.y - m.y));
 #pragma unroll
                     for (int d = 0; d < D; ++d) g[d] = fmaf((float)L::e(a, d), dd, g[d]);
@@ -240,26 +262,32 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
         for (int d = 0; d < D; ++d) u[d] = fmaf(0.5f, Fs[d], j[d]) * irt;
         const float u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        __syncthreads();  // the mu tiles are read
 #pragma unroll 1
-        for (int i = 0; i < NC; ++i) {
-            __syncthreads();
-            const float *rhi = rh + (long long)i * N, *rli = rl + (long long)i * N;
+        for (int i = 0; i < NC; ++i)
 #pragma unroll
             for (int q = 0; q < KPT; ++q)
-                if (t + q * kThreads < TL::HN) RT[t + q * kThreads] = __ldg(rhi + gk[q]) + __ldg(rli + gk[q]);
-            __syncthreads();
-            if (!active) continue;
+                if (t + q * kThreads < TL::HN) {
+                    cp_async4(RH + i * TL::HN + t + q * kThreads, rh + (long long)i * N + gk[q]);
+                    cp_async4(RL + i * TL::HN + t + q * kThreads, rl + (long long)i * N + gk[q]);
+                }
+        cp_async_wait_all();
+        __syncthreads();
+        if (!active) continue;
+#pragma unroll 1
+        for (int i = 0; i < NC; ++i) {
+            const float *rhi = RH + i * TL::HN, *rli = RL + i * TL::HN;
             // grad rho_i from the neighbours' pairs (binary32)
             float G[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
             for (int a = 1; a < Q; a += 2) {
-                const float p = RT[ti + toff[a]];
-                const float m = RT[ti + toff[a + 1]];
+                const float p = rhi[ti + toff[a]] + rli[ti + toff[a]];
+                const float m = rhi[ti + toff[a + 1]] + rli[ti + toff[a + 1]];
                 const float dd = 3.0f * (float)L::w(a) * (p - m);
 #pragma unroll
                 for (int d = 0; d < D; ++d) G[d] = fmaf((float)L::e(a, d), dd, G[d]);
             }
-            const float ri = RT[ti];
+            const float ri = rhi[ti] + rli[ti];
             float F[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
             for (int d = 0; d < D; ++d) F[d] = FS[(i * 3 + d) * kThreads + t];
