@@ -20,8 +20,6 @@
 // k_mp_psi forms psi after an initialisation.
 #pragma once
 
-#include <algorithm>
-
 #include "lbm_internal.h"
 #include "lbm_thermo_df.cuh"
 
@@ -115,146 +113,60 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-// A CTA of k_mp_collide owns a block of TX x TY x TZ nodes (one per thread)
-// and stages the mu_i of every component for the block and its one-node halo
-// in shared memory (asynchronous copies, all in flight at once), then the
-// density pairs in the same space, so each neighbour value is read from L2
-// about once instead of once per neighbour.
-template <int LAT> struct MpTile {
-    static constexpr int TX = 32, TY = LAT == 0 ? 8 : 4, TZ = LAT == 0 ? 1 : 2;
-    static constexpr int HX = TX + 2, HY = TY + 2, HZ = LAT == 0 ? 1 : TZ + 2;
-    static constexpr int HN = HX * HY * HZ;
-    static_assert(TX * TY * TZ == kThreads, "one node per thread");
-};
-
-template <int LAT, int NC> constexpr size_t mp_collide_smem()
-{
-    // forces, then one space for mu [NC][HN] (float2) or the pairs [2][NC][HN] (float)
-    return (size_t)NC * 3 * kThreads * sizeof(float) + (size_t)NC * MpTile<LAT>::HN * sizeof(float2);
-}
-
-// cp.async of 4 or 8 bytes from global to shared memory (both aligned to the size)
-__device__ __forceinline__ void cp_async4(void *sdst, const void *gsrc)
-{
-    const unsigned a = (unsigned)__cvta_generic_to_shared(sdst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(a), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void *sdst, const void *gsrc)
-{
-    const unsigned a = (unsigned)__cvta_generic_to_shared(sdst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(a), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all()
-{
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
-
-__device__ __forceinline__ int wrap_any(int v, int n)
-{
-    if (v < 0) return v + n;  // v >= -1
-    return v < n ? v : v % n;
-}
-
 template <int LAT, int NC>
 __global__ void __launch_bounds__(kThreads)
     k_mp_collide(const Params P, StateBufs in, StateBufs out, const float2 *__restrict__ mu,
                  float *__restrict__ osum, float *__restrict__ ocmp)
 {
     using L = Lattice<LAT>;
-    using TL = MpTile<LAT>;
     constexpr int D = L::D, Q = L::Q, NS = Q - 1;
-    extern __shared__ __align__(16) unsigned char smem[];
-    float *FS = (float *)smem;                        // [NC * 3][kThreads] this thread's forces F_i
-    float2 *MT = (float2 *)(FS + NC * 3 * kThreads);  // [NC][HN] mu_i of the block and halo
-    float *RH = (float *)MT;                          // [NC][HN] rho_i hi (after the forces)
-    float *RL = RH + NC * TL::HN;                     // [NC][HN] rho_i lo
+    __shared__ float FS[NC * 3][kThreads];  // this thread's forces F_i
     const float *gin = (const float *)in.g;
     float *gout = (float *)out.g;
     const float *rh = in.rhi_f();
     const float *rl = in.rlo;
-    const int nx = P.nx, ny = P.ny, nz = P.nz;
     const int N = (int)P.N;
     const int t = threadIdx.x;
-    const int tx = t % TL::TX, ty = (t / TL::TX) % TL::TY, tz = t / (TL::TX * TL::TY);
-    const int nbx = (nx + TL::TX - 1) / TL::TX, nby = (ny + TL::TY - 1) / TL::TY, nbz = (nz + TL::TZ - 1) / TL::TZ;
-    const int nblk = nbx * nby * nbz;
-    // tile offset of each direction and of this thread's node
-    int toff[Q];
-#pragma unroll
-    for (int a = 0; a < Q; ++a) toff[a] = L::e(a, 0) + TL::HX * (L::e(a, 1) + TL::HY * L::e(a, 2));
-    const int ti = (tx + 1) + TL::HX * ((ty + 1) + TL::HY * (tz + (TL::HZ > 1 ? 1 : 0)));
     const float om = (float)P.omega, om1 = (float)(1.0 - P.omega), cF = (float)(1.0 - 0.5 * P.omega);
-    for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-        const int bx = blk % nbx, by = (blk / nbx) % nby, bz = blk / (nbx * nby);
-        const int x0 = bx * TL::TX, y0 = by * TL::TY, z0 = bz * TL::TZ;
-        const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
-        const bool active = x < nx && y < ny && z < nz;
-        const int r = active ? x + nx * (y + ny * z) : 0;
-        // the tile's node index for tile entry k (periodic; any block size)
-        auto gnode = [&](int k) {
-            const int hx = k % TL::HX, hy = (k / TL::HX) % TL::HY, hz = k / (TL::HX * TL::HY);
-            const int gx = wrap_any(x0 + hx - 1, nx), gy = wrap_any(y0 + hy - 1, ny);
-            const int gz = TL::HZ > 1 ? wrap_any(z0 + hz - 1, nz) : z0;
-            return gx + nx * (gy + ny * gz);
-        };
-        // the node of each tile entry this thread loads, once per block
-        constexpr int KPT = (TL::HN + kThreads - 1) / kThreads;
-        int gk[KPT];
-#pragma unroll
-        for (int q = 0; q < KPT; ++q) {
-            const int k = t + q * kThreads;
-            gk[q] = k < TL::HN ? gnode(k) : 0;
-        }
+    for (int r = blockIdx.x * blockDim.x + t; r < N; r += gridDim.x * blockDim.x) {
         int nb[Q];
         neighbours<LAT>(P, r, nb);
         // momentum sum_i sum_a e_a g_a and the total density
         float j[3] = {0.0f, 0.0f, 0.0f}, rt = 0.0f;
-        if (active) {
 #pragma unroll
-            for (int i = 0; i < NC; ++i) {
-                const float *gi = gin + (long long)i * NS * N;
+        for (int i = 0; i < NC; ++i) {
+            const float *gi = gin + (long long)i * NS * N;
 #pragma unroll
-                for (int a = 1; a < Q; ++a) {
-                    const float v = __ldg(gi + (long long)(a - 1) * N + r);
+            for (int a = 1; a < Q; ++a) {
+                const float v = __ldg(gi + (long long)(a - 1) * N + r);
 #pragma unroll
-                    for (int d = 0; d < D; ++d)
-                        if (L::e(a, d) > 0) j[d] += v;
-                        else if (L::e(a, d) < 0) j[d] -= v;
-                }
-                rt += __ldg(rh + (long long)i * N + r) + __ldg(rl + (long long)i * N + r);
+                for (int d = 0; d < D; ++d)
+                    if (L::e(a, d) > 0) j[d] += v;
+                    else if (L::e(a, d) < 0) j[d] -= v;
             }
+            rt += __ldg(rh + (long long)i * N + r) + __ldg(rl + (long long)i * N + r);
         }
         // Eq. (5): F_i = -rho~_i grad mu_i; grad X = 3 sum_pairs w e (X(r+e) - X(r-e)),
         // each difference on the (hi, lo) pairs rounded once
         float Fs[3] = {0.0f, 0.0f, 0.0f};
-        __syncthreads();  // the previous block's readers of the tiles are done
-#pragma unroll 1
-        for (int i = 0; i < NC; ++i)
+#pragma unroll 2
+        for (int i = 0; i < NC; ++i) {
+            const float2 *mi = mu + (long long)i * N;
+            float g[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
-            for (int q = 0; q < KPT; ++q)
-                if (t + q * kThreads < TL::HN) cp_async8(MT + i * TL::HN + t + q * kThreads, mu + (long long)i * N + gk[q]);
-        cp_async_wait_all();
-        __syncthreads();
-        if (active) {
-#pragma unroll 1
-            for (int i = 0; i < NC; ++i) {
-                const float2 *mt = MT + i * TL::HN;
-                float g[3] = {0.0f, 0.0f, 0.0f};
+            for (int a = 1; a < Q; a += 2) {  // (a, a+1) opposite
+                const float2 p = __ldg(mi + nb[a]), m = __ldg(mi + nb[a + 1]);
+                const float dd = 3.0f * (float)L::w(a) * ((p.x - m.x) + (p.y - m.y));
 #pragma unroll
-                for (int a = 1; a < Q; a += 2) {  // (a, a+1) opposite
-                    const float2 p = mt[ti + toff[a]], m = mt[ti + toff[a + 1]];
-                    const float dd = 3.0f * (float)L::w(a) * ((p.x - m.x) + (p.y - m.y));
+                for (int d = 0; d < D; ++d) g[d] = fmaf((float)L::e(a, d), dd, g[d]);
+            }
+            const float ri = __ldg(rh + (long long)i * N + r) + __ldg(rl + (long long)i * N + r);
+            const float rmi = ri * PV<float>::invM(P, i);
 #pragma unroll
-                    for (int d = 0; d < D; ++d) g[d] = fmaf((float)L::e(a, d), dd, g[d]);
-                }
-                const float ri = __ldg(rh + (long long)i * N + r) + __ldg(rl + (long long)i * N + r);
-                const float rmi = ri * PV<float>::invM(P, i);
-#pragma unroll
-                for (int d = 0; d < D; ++d) {
-                    const float f = -rmi * g[d];
-                    FS[(i * 3 + d) * kThreads + t] = f;
-                    Fs[d] += f;
-                }
+            for (int d = 0; d < D; ++d) {
+                const float f = -rmi * g[d];
+                FS[i * 3 + d][t] = f;
+                Fs[d] += f;
             }
         }
         const float irt = __fdividef(1.0f, rt);
@@ -262,35 +174,23 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
         for (int d = 0; d < D; ++d) u[d] = fmaf(0.5f, Fs[d], j[d]) * irt;
         const float u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-        __syncthreads();  // the mu tiles are read
-#pragma unroll 1
-        for (int i = 0; i < NC; ++i)
-#pragma unroll
-            for (int q = 0; q < KPT; ++q)
-                if (t + q * kThreads < TL::HN) {
-                    cp_async4(RH + i * TL::HN + t + q * kThreads, rh + (long long)i * N + gk[q]);
-                    cp_async4(RL + i * TL::HN + t + q * kThreads, rl + (long long)i * N + gk[q]);
-                }
-        cp_async_wait_all();
-        __syncthreads();
-        if (!active) continue;
 #pragma unroll 1
         for (int i = 0; i < NC; ++i) {
-            const float *rhi = RH + i * TL::HN, *rli = RL + i * TL::HN;
+            const float *rhi = rh + (long long)i * N, *rli = rl + (long long)i * N;
             // grad rho_i from the neighbours' pairs (binary32)
             float G[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
             for (int a = 1; a < Q; a += 2) {
-                const float p = rhi[ti + toff[a]] + rli[ti + toff[a]];
-                const float m = rhi[ti + toff[a + 1]] + rli[ti + toff[a + 1]];
+                const float p = __ldg(rhi + nb[a]) + __ldg(rli + nb[a]);
+                const float m = __ldg(rhi + nb[a + 1]) + __ldg(rli + nb[a + 1]);
                 const float dd = 3.0f * (float)L::w(a) * (p - m);
 #pragma unroll
                 for (int d = 0; d < D; ++d) G[d] = fmaf((float)L::e(a, d), dd, G[d]);
             }
-            const float ri = rhi[ti] + rli[ti];
+            const float ri = __ldg(rhi + r) + __ldg(rli + r);
             float F[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
-            for (int d = 0; d < D; ++d) F[d] = FS[(i * 3 + d) * kThreads + t];
+            for (int d = 0; d < D; ++d) F[d] = FS[i * 3 + d][t];
             float Fu = 0.0f, Gu = 0.0f;
 #pragma unroll
             for (int d = 0; d < D; ++d) {
@@ -387,17 +287,8 @@ template <int LAT, int NC> struct Impl {
         kt_begin(kt, kKtMpMu, s);
         k_mp_mu<LAT, NC><<<G, kThreads, sm, s>>>(P, in, ps, mu);
         kt_end(kt, s);
-        using TL = MpTile<LAT>;
-        const long long nblk = (long long)((P.nx + TL::TX - 1) / TL::TX) * ((P.ny + TL::TY - 1) / TL::TY) *
-                               ((P.nz + TL::TZ - 1) / TL::TZ);
-        const unsigned GC = (unsigned)std::min<long long>(nblk, 152LL * 16);
-        const size_t smc = mp_collide_smem<LAT, NC>();
-        if (smc > 48 * 1024 &&
-            cudaFuncSetAttribute(k_mp_collide<LAT, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc) !=
-                cudaSuccess)
-            return (int)cudaGetLastError();
         kt_begin(kt, kKtMpCollide, s);
-        k_mp_collide<LAT, NC><<<GC, kThreads, smc, s>>>(P, in, out, mu, osum, ocmp);
+        k_mp_collide<LAT, NC><<<G, kThreads, 0, s>>>(P, in, out, mu, osum, ocmp);
         kt_end(kt, s);
         kt_begin(kt, kKtMpUpdate, s);
         k_mp_update<LAT, NC><<<G, kThreads, 0, s>>>(P, in, out, osum, ocmp, ps);
