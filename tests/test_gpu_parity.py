@@ -302,8 +302,8 @@ def test_multipass_several_steps(lattice, shape, nc, steps):
     """The multi-pass schedule (density update and psi of the next step in one
     pass) against the oracle over several steps: within 2e-6 of max |g_i|
     per step (a few binary32 roundings per step on each population).  The
-    shapes cover collide blocks (32 x 4 x 2 nodes in 3D, 32 x 8 in 2D) that
-    are ragged in every direction and boxes smaller than one block."""
+    shapes include boxes whose rows are longer than one warp and ragged
+    against the 256-node CTAs, and boxes smaller than one CTA."""
     err = one_step_case(300 + nc, nc, lattice, shape, precision=FP32DEV, schedule=MULTIPASS, nsteps=steps)
     assert err < 2e-6 * steps, err
 
