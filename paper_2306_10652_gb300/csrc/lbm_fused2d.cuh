@@ -418,11 +418,13 @@ __global__ void __launch_bounds__(kT) k_mu32(const Params P, const int W, const 
     }
     const df::TabSplit LT{LV, LL};
     float ph[NC], pl[NC];  // density pairs of row k-1 at this column
+    df::F2 Bp = {0.0f, 0.0f};  // and its B (Eq. 11)
 #pragma unroll
     for (int i = 0; i < NC; ++i) ph[i] = pl[i] = 0.0f;
     for (int kk = 0; kk < h + 4; ++kk) {
         const int k = y0 - 2 + kk;
         float hh[NC], ll[NC];
+        df::F2 Bk = {0.0f, 0.0f};
         if (hasP) {
             const IDX rb = (IDX)wrapc(k, ny) * (IDX)nx + (IDX)xg;
 #pragma unroll
@@ -430,7 +432,8 @@ __global__ void __launch_bounds__(kT) k_mu32(const Params P, const int W, const 
                 hh[i] = __ldg(rhin + i * N + rb);
                 ll[i] = __ldg(rlin + i * N + rb);
             }
-            const df::F2 ps = df::psi<NC>(P, hh, ll);
+            df::F2 ps;
+            df::psi_and_B<NC>(P, hh, ll, ps, Bk);
             PS[(kk % 3) * kT + t] = make_float2(ps.hi, ps.lo);
         }
         __syncthreads();
@@ -440,7 +443,7 @@ __global__ void __launch_bounds__(kT) k_mu32(const Params P, const int W, const 
                                         df::f2(p0[t]), df::f2(p2[t + 1]), df::f2(p2[t - 1]), df::f2(p0[t + 1]),
                                         df::f2(p0[t - 1]));
             float2 *out = MU + ((kk - 1) % 3) * NC * kT + t;
-            df::mu_rolled<NC>(P, LT, ph, pl, lap, PHs + t, PLs + t, out, kT, out, kT);
+            df::mu_rolled<NC>(P, LT, ph, pl, Bp, lap, PHs + t, PLs + t, out, kT, out, kT);
         }
         if (hasP) {
 #pragma unroll
@@ -448,6 +451,7 @@ __global__ void __launch_bounds__(kT) k_mu32(const Params P, const int W, const 
                 ph[i] = hh[i];
                 pl[i] = ll[i];
             }
+            Bp = Bk;
         }
         __syncthreads();
         if (kk >= 4 && interior) {
@@ -460,14 +464,17 @@ __global__ void __launch_bounds__(kT) k_mu32(const Params P, const int W, const 
                 const float2 *s0 = S + i * kT, *c0 = C + i * kT, *n0 = Nr + i * kT;
                 const float2 e1 = c0[t + 1], w1 = c0[t - 1], n1 = n0[t], s1 = s0[t];
                 const float2 ne = n0[t + 1], sw = s0[t - 1], se = s0[t + 1], nw = n0[t - 1];
-                const float dE = (e1.x - w1.x) + (e1.y - w1.y);
-                const float dN = (n1.x - s1.x) + (n1.y - s1.y);
-                const float dNE = (ne.x - sw.x) + (ne.y - sw.y);
-                const float dSE = (se.x - nw.x) + (se.y - nw.y);
-                // grad X = 3 sum_pairs w e (X(r+e) - X(r-e)): faces 1/9, diagonals 1/36
-                const float gx = 3.0f * fmaf(1.0f / 9.0f, dE, (1.0f / 36.0f) * (dNE + dSE));
-                const float gy = 3.0f * fmaf(1.0f / 9.0f, dN, (1.0f / 36.0f) * (dNE - dSE));
-                G[i * N + ob] = make_float2(gx, gy);
+                // each difference on the (hi, lo) pairs (one packed subtraction), rounded once
+                const float2 vE = df::vsub(e1, w1), vN = df::vsub(n1, s1);
+                const float2 vNE = df::vsub(ne, sw), vSE = df::vsub(se, nw);
+                const float dE = vE.x + vE.y, dN = vN.x + vN.y, dNE = vNE.x + vNE.y, dSE = vSE.x + vSE.y;
+                // grad X = 3 sum_pairs w e (X(r+e) - X(r-e)): faces 1/9, diagonals 1/36;
+                // lanes (d/dx, d/dy)
+                const float2 g = df::vmul(df::vbc(3.0f),
+                                          df::vfma(df::vbc(1.0f / 9.0f), make_float2(dE, dN),
+                                                   df::vmul(df::vbc(1.0f / 36.0f),
+                                                            df::vadd(df::vbc(dNE), make_float2(dSE, -dSE)))));
+                G[i * N + ob] = g;
             }
         }
     }

@@ -109,7 +109,8 @@ __global__ void __launch_bounds__(kThreads)
             h[i] = __ldg(st.rhi_f() + (long long)i * N + r);
             l[i] = __ldg(st.rlo + (long long)i * N + r);
         }
-        df::mu_rolled<NC>(P, df::TabF4{LT}, h, l, lapQ<LAT>(psi, nb), PH + t, PL + t, TS + t, kThreads, mu + r, N);
+        df::mu_rolled<NC>(P, df::TabF4{LT}, h, l, df::mix_B<NC>(P, h, l), lapQ<LAT>(psi, nb), PH + t, PL + t, TS + t,
+                          kThreads, mu + r, N);
     }
 }
 

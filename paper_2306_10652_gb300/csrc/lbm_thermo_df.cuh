@@ -188,17 +188,55 @@ __device__ __forceinline__ void mu(const Params &P, const float4 *__restrict__ t
     }
 }
 
+// B = b_m rho~ = sum_j (b_j / M_j) rho_j at one node (Eq. 11), as mu() forms it
+template <int NC>
+__device__ __forceinline__ F2 mix_B(const Params &P, const float (&h)[NC], const float (&l)[NC])
+{
+    DotPos bd;
+    bd.first(f2(P.dB[0]), {h[0], l[0]});
+#pragma unroll
+    for (int j = 1; j < NC; ++j) bd.add(f2(P.dB[j]), {h[j], l[j]});
+    return bd.value();
+}
+
+// psi (Eq. 4) and B (Eq. 11) of one node in one packed sum: lane x is psi<NC>,
+// lane y is mix_B<NC>, each with the operations of the scalar form.
+template <int NC>
+__device__ __forceinline__ void psi_and_B(const Params &P, const float (&h)[NC], const float (&l)[NC], F2 &psi,
+                                          F2 &B)
+{
+    Dot2x t;
+    t.first(P.dPBp[0], h[0], l[0]);
+#pragma unroll
+    for (int j = 1; j < NC; ++j) t.add(P.dPBp[j], h[j], l[j]);
+    psi = fast_two_sum(t.s.x, t.c.x);
+    B = fast_two_sum(t.s.y, t.c.y);
+}
+
+__device__ __forceinline__ F2x2 mul_u2(F2x2 a, F2x2 b)
+{
+    const F2x2 p = two_prod2(a.hi, b.hi);
+    return {p.hi, vfma(a.hi, b.lo, vfma(a.lo, b.hi, p.lo))};
+}
+__device__ __forceinline__ F2x2 bc2(F2 a) { return {vbc(a.hi), vbc(a.lo)}; }
+__device__ __forceinline__ F2x2 lanes(float4 v) { return {make_float2(v.x, v.y), make_float2(v.z, v.w)}; }
+__device__ __forceinline__ F2x2 neg2(F2x2 a) { return {vneg(a.hi), vneg(a.lo)}; }
+
 // mu of one node with rolled loops over the row pairs of T_i and over the
 // components (the unrolled form above is a few thousand instructions of
 // straight-line code at Nc = 10, more than the instruction cache holds).
-// The same operations in the same order, so the result is bitwise that of
-// mu().  Per-thread scratch in shared memory with stride `pitch`: PH, PL [NC]
-// floats (the density pair) and TS [NC] float2 (T_i); mu_i is written to
-// out[i * ostride].  TS may be out itself (same stride): iteration i reads
-// T_i before it stores mu_i.  Tab: a view of the log table (lbm_df64.cuh).
+// Components 2q and 2q+1 go through one iteration on the packed FP32x2
+// units, each lane with the operations of mu(), so the result is bitwise
+// that of mu().  B (Eq. 11, from mix_B or psi_and_B) comes in.  Per-thread
+// scratch in shared memory with stride `pitch`: PH, PL [NC] floats (the
+// density pair) and TS [NC] float2 holding T_i, with the pair q stored as
+// TS[2q] = (hi_2q, hi_2q+1), TS[2q+1] = (lo_2q, lo_2q+1) and an odd last
+// component as (hi, lo).  mu_i is written to out[i * ostride]; TS may be
+// out itself (same stride): iteration q reads T_2q, T_2q+1 before it stores
+// their mu.  Tab: a view of the log table (lbm_df64.cuh).
 template <int NC, typename Tab>
 __device__ __forceinline__ void mu_rolled(const Params &P, Tab tab, const float (&h)[NC], const float (&l)[NC],
-                                          F2 lap, float *PH, float *PL, float2 *TS, int pitch, float2 *out,
+                                          F2 B, F2 lap, float *PH, float *PL, float2 *TS, int pitch, float2 *out,
                                           int ostride)
 {
     constexpr double kS2 = 1.41421356237309504880168872421;
@@ -217,20 +255,15 @@ __device__ __forceinline__ void mu_rolled(const Params &P, Tab tab, const float 
         }
     }
     const F2 rho = rt.value();
-    DotPos bd;
-    bd.first(f2(P.dB[0]), {h[0], l[0]});
-#pragma unroll
-    for (int j = 1; j < NC; ++j) bd.add(f2(P.dB[j]), {h[j], l[j]});
-    const F2 B = bd.value();
 #pragma unroll 1
     for (int r = 0; r < NC / 2; ++r) {
         Dot2x t;
         t.first(P.dAp[r * kMaxNc], h[0], l[0]);
 #pragma unroll
         for (int j = 1; j < NC; ++j) t.add(P.dAp[r * kMaxNc + j], h[j], l[j]);
-        const F2 a = fast_two_sum(t.s.x, t.c.x), b = fast_two_sum(t.s.y, t.c.y);
-        TS[(2 * r) * pitch] = make_float2(a.hi, a.lo);
-        TS[(2 * r + 1) * pitch] = make_float2(b.hi, b.lo);
+        const F2x2 v = fast_two_sum2(t.s, t.c);  // fast_two_sum lane by lane
+        TS[(2 * r) * pitch] = v.hi;
+        TS[(2 * r + 1) * pitch] = v.lo;
     }
     if constexpr (NC % 2 == 1) {
         DotPos t;
@@ -240,10 +273,16 @@ __device__ __forceinline__ void mu_rolled(const Params &P, Tab tab, const float 
         const F2 v = t.value();
         TS[(NC - 1) * pitch] = make_float2(v.hi, v.lo);
     }
+    // T_i in the layout above
+    auto Ti = [&](int i) -> F2 {
+        if (NC % 2 == 1 && i == NC - 1) return f2(TS[i * pitch]);
+        const float2 a = TS[(i & ~1) * pitch], b = TS[((i & ~1) + 1) * pitch];
+        return (i & 1) ? F2{a.y, b.y} : F2{a.x, b.x};
+    };
     DotPos qd;
-    qd.first(y[0], f2(TS[0]));
+    qd.first(y[0], Ti(0));
 #pragma unroll
-    for (int i = 1; i < NC; ++i) qd.add(y[i], f2(TS[i * pitch]));
+    for (int i = 1; i < NC; ++i) qd.add(y[i], Ti(i));
     const F2 Q = qd.value();
     const F2 one = {1.0f, 0.0f};
     const F2 omB = add(one, neg(B));
@@ -259,8 +298,25 @@ __device__ __forceinline__ void mu_rolled(const Params &P, Tab tab, const float 
                        mul(mul(Q, u), add(mul(Lu, {hi_of(0.5 / kS2), lo_of(0.5 / kS2)}), neg(w))));
     const F2 RC2 = mul(Lu, {hi_of(-1.0 / kS2), lo_of(-1.0 / kS2)});
     const F2 RG = mul(RT, lnomB);
+    const F2x2 RT2 = bc2(RT), nRG2 = bc2(neg(RG)), RC12 = bc2(RC1), RC22 = bc2(RC2), lap2 = bc2(lap);
 #pragma unroll 1
-    for (int i = 0; i < NC; ++i) {
+    for (int q = 0; q < NC / 2; ++q) {
+        const F2x2 x = {make_float2(PH[(2 * q) * pitch], PH[(2 * q + 1) * pitch]),
+                        make_float2(PL[(2 * q) * pitch], PL[(2 * q + 1) * pitch])};
+        const F2x2 T = {TS[(2 * q) * pitch], TS[(2 * q + 1) * pitch]};
+        Dot2 a;
+        a.start(mul_u2(RT2, log2x(x, tab)));
+        a.add_term(lanes(P.dRKp[q]));
+        a.add_term(nRG2);
+        a.add_term(mul_u2(lanes(P.dbp[q]), RC12));
+        a.add_term(mul_u2(T, RC22));
+        a.add_term(neg2(mul_u2(lanes(P.dsqkp[q]), lap2)));
+        const F2x2 m = a.value();
+        out[(long long)(2 * q) * ostride] = make_float2(m.hi.x, m.lo.x);
+        out[(long long)(2 * q + 1) * ostride] = make_float2(m.hi.y, m.lo.y);
+    }
+    if constexpr (NC % 2 == 1) {
+        constexpr int i = NC - 1;
         Dot a;
         const F2 t0 = mul_u(RT, log({PH[i * pitch], PL[i * pitch]}, tab));
         a.s = t0.hi;
