@@ -50,27 +50,27 @@ struct Dot2x {
     {
         const float2 X = make_float2(xh, xh), XL = make_float2(xl, xl);
         const float2 ch = make_float2(A.x, A.y), cl = make_float2(A.z, A.w);
-        const float2 p = __fmul2_rn(ch, X);
-        const float2 pe = __ffma2_rn(ch, X, pneg(p));
+        const float2 p = vmul(ch, X);
+        const float2 pe = vfma(ch, X, pneg(p));
         s = p;
-        c = __ffma2_rn(ch, XL, __ffma2_rn(cl, X, pe));
+        c = vfma(ch, XL, vfma(cl, X, pe));
     }
     __device__ __forceinline__ void add(float4 A, float xh, float xl)
     {
         const float2 X = make_float2(xh, xh), XL = make_float2(xl, xl);
         const float2 ch = make_float2(A.x, A.y), cl = make_float2(A.z, A.w);
-        const float2 p = __fmul2_rn(ch, X);
-        const float2 pe = __ffma2_rn(ch, X, pneg(p));
+        const float2 p = vmul(ch, X);
+        const float2 pe = vfma(ch, X, pneg(p));
         // TwoSum(s, p) lane by lane, as FastTwoSum of the larger and the
         // smaller (both non-negative: see two_sum_pos)
         const int sx = __float_as_int(s.x), sy = __float_as_int(s.y);
         const int px = __float_as_int(p.x), py = __float_as_int(p.y);
         const float2 big = make_float2(__int_as_float(max(sx, px)), __int_as_float(max(sy, py)));
         const float2 small = make_float2(__int_as_float(min(sx, px)), __int_as_float(min(sy, py)));
-        const float2 t = __fadd2_rn(big, small);
-        const float2 e = __fadd2_rn(small, pneg(__fadd2_rn(t, pneg(big))));
+        const float2 t = vadd(big, small);
+        const float2 e = vadd(small, pneg(vadd(t, pneg(big))));
         s = t;
-        c = __fadd2_rn(c, __fadd2_rn(e, __ffma2_rn(ch, XL, __ffma2_rn(cl, X, pe))));
+        c = vadd(c, vadd(e, vfma(ch, XL, vfma(cl, X, pe))));
     }
 };
 
