@@ -256,14 +256,6 @@ void refresh_float_params(Params &P)
             P.dAp[r * kMaxNc + j] = make_float4(a.x, b.x, a.y, b.y);
         }
     P.dRT = split2(P.RT);
-    for (int q = 0; q < kMaxNc / 2; ++q) {
-        auto pair = [&](const float2 *v) {
-            return make_float4(v[2 * q].x, v[2 * q + 1].x, v[2 * q].y, v[2 * q + 1].y);
-        };
-        P.dRKp[q] = pair(P.dRK);
-        P.dbp[q] = pair(P.db);
-        P.dsqkp[q] = pair(P.dsqk);
-    }
     for (int j = 0; j < kMaxNc; ++j) P.dPBp[j] = make_float4(P.dPk[j].x, P.dB[j].x, P.dPk[j].y, P.dB[j].y);
     df::make_log_table(&P.logtab[0].x);
 }

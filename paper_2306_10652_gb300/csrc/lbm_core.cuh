@@ -83,8 +83,6 @@ struct Params {
     float2 dsqk[kMaxNc];         // sqrt(kappa_i)
     float2 dPk[kMaxNc];          // sqrt(kappa_j) / M_j
     float2 dRT;                  // RT
-    // components 2q, 2q+1 side by side, (hi_2q, hi_2q+1, lo_2q, lo_2q+1), for the packed FP32x2 units
-    float4 dRKp[kMaxNc / 2], dbp[kMaxNc / 2], dsqkp[kMaxNc / 2];
     float4 dPBp[kMaxNc];         // (dPk_j hi, dB_j hi, dPk_j lo, dB_j lo): psi and B in one packed sum
     float4 logtab[128];          // df64 logarithm table (lbm_df64.cuh)
 };

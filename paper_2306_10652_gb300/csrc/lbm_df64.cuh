@@ -238,19 +238,12 @@ __device__ __forceinline__ F2 log(F2 x, Tab tab)
 
 __device__ __forceinline__ F2 log(F2 x, const float4 *__restrict__ tab) { return log(x, TabF4{tab}); }
 
-// ---- two df64 values side by side on the packed FP32x2 units ----------------
-// Lane x and lane y each take exactly the operations of the scalar routine of
-// the same name above (a - b as a + (-b), which rounds the same), so each lane
-// gives the scalar result bit for bit; one packed instruction issues the work
-// of two.
-struct F2x2 {
-    float2 hi, lo;
-};
-
-// The packed operations are written in PTX with an explicit rounding mode, so
-// that no compiler pass fuses a product into a following sum (the scalar
-// routines get the same guarantee from __fmul_rn and __fadd_rn); measured on
-// GB300, the fused form changes the error-free transformations' results.
+// ---- packed FP32x2 operations --------------------------------------------------
+// One instruction does the binary32 operation on both lanes, each rounded as
+// the scalar operation rounds it.  They are written in PTX with an explicit
+// rounding mode, so that no compiler pass fuses a product into a following
+// sum: the error-free transformations built on them need the same guarantee
+// that __fmul_rn and __fadd_rn give the scalar routines.
 __device__ __forceinline__ float2 vbc(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }
 __device__ __forceinline__ float2 vadd(float2 a, float2 b)
@@ -280,81 +273,6 @@ __device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c)
         : "=f"(d.x), "=f"(d.y)
         : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
     return d;
-}
-
-__device__ __forceinline__ F2x2 two_sum2(float2 a, float2 b)
-{
-    const float2 s = vadd(a, b);
-    const float2 bp = vsub(s, a);
-    return {s, vadd(vsub(a, vsub(s, bp)), vsub(b, bp))};
-}
-
-__device__ __forceinline__ F2x2 fast_two_sum2(float2 a, float2 b)  // |a| >= |b| lane by lane
-{
-    const float2 s = vadd(a, b);
-    return {s, vsub(b, vsub(s, a))};
-}
-
-// two_sum_pos lane by lane (both operands non-negative)
-__device__ __forceinline__ F2x2 two_sum_pos2(float2 a, float2 b)
-{
-    const int ax = __float_as_int(a.x), ay = __float_as_int(a.y);
-    const int bx = __float_as_int(b.x), by = __float_as_int(b.y);
-    const float2 big = make_float2(__int_as_float(max(ax, bx)), __int_as_float(max(ay, by)));
-    const float2 small = make_float2(__int_as_float(min(ax, bx)), __int_as_float(min(ay, by)));
-    const float2 s = vadd(big, small);
-    return {s, vsub(small, vsub(s, big))};
-}
-
-__device__ __forceinline__ F2x2 two_prod2(float2 a, float2 b)
-{
-    const float2 p = vmul(a, b);
-    return {p, vfma(a, b, vneg(p))};
-}
-
-// Dot lane by lane: Dot::first, Dot::add_term and Dot::value
-struct Dot2 {
-    float2 s, c;
-    __device__ __forceinline__ void start(F2x2 t)
-    {
-        s = t.hi;
-        c = t.lo;
-    }
-    __device__ __forceinline__ void add_term(F2x2 t)
-    {
-        const F2x2 u = two_sum2(s, t.hi);
-        s = u.hi;
-        c = vadd(c, vadd(u.lo, t.lo));
-    }
-    __device__ __forceinline__ F2x2 value() const { return fast_two_sum2(s, c); }
-};
-
-// log lane by lane
-template <typename Tab>
-__device__ __forceinline__ F2x2 log2x(F2x2 x, Tab tab)
-{
-    const int ux = __float_as_int(x.hi.x), uy = __float_as_int(x.hi.y);
-    const float2 kf = vsub(make_float2(__int_as_float(0x4b000000 + (ux >> 23)), __int_as_float(0x4b000000 + (uy >> 23))),
-                           vbc(8388608.0f + 127.0f));
-    const float2 m = make_float2(__int_as_float((ux & 0x007fffff) | 0x3f800000),
-                                 __int_as_float((uy & 0x007fffff) | 0x3f800000));
-    const float3 ta = tab[(ux >> 16) & 0x7f], tb = tab[(uy >> 16) & 0x7f];
-    const F2x2 P = two_prod2(m, make_float2(ta.x, tb.x));
-    const float2 r = vsub(P.hi, vbc(1.0f));  // exact
-    const float2 corr = vfma(P.lo, make_float2(rcp_approx(P.hi.x), rcp_approx(P.hi.y)),
-                             vmul(x.lo, make_float2(rcp_approx(x.hi.x), rcp_approx(x.hi.y))));
-    const F2x2 r2 = two_prod2(r, r);
-    const float2 r3 = vmul(r2.hi, r);
-    const float2 tail = vmul(r3, vfma(r, vfma(r, vbc(0.2f), vbc(-0.25f)), vbc(0.333333343f)));
-    const F2x2 h = fast_two_sum2(r, vmul(vbc(-0.5f), r2.hi));
-    const F2x2 kl = two_prod2(kf, vbc(hi_of(kLn2)));
-    const F2x2 big = two_sum2(kl.hi, make_float2(ta.y, tb.y));
-    const F2x2 s = two_sum2(big.hi, h.hi);
-    const float2 lo = vadd(vadd(vadd(big.lo, s.lo), vadd(h.lo, make_float2(ta.z, tb.z))),
-                           vadd(vfma(kf, vbc(lo_of(kLn2)), kl.lo), vfma(vbc(-0.5f), r2.lo, vadd(tail, corr))));
-    const bool okx = x.hi.x >= 1.17549435e-38f && x.hi.x <= 3.40282347e38f;
-    const bool oky = x.hi.y >= 1.17549435e-38f && x.hi.y <= 3.40282347e38f;
-    return {make_float2(okx ? s.hi.x : __int_as_float(0x7fc00000), oky ? s.hi.y : __int_as_float(0x7fc00000)), lo};
 }
 
 // Host: fill the log table (binary64 arithmetic; called once per problem).

@@ -464,17 +464,14 @@ __global__ void __launch_bounds__(kT) k_mu32(const Params P, const int W, const 
                 const float2 *s0 = S + i * kT, *c0 = C + i * kT, *n0 = Nr + i * kT;
                 const float2 e1 = c0[t + 1], w1 = c0[t - 1], n1 = n0[t], s1 = s0[t];
                 const float2 ne = n0[t + 1], sw = s0[t - 1], se = s0[t + 1], nw = n0[t - 1];
-                // each difference on the (hi, lo) pairs (one packed subtraction), rounded once
-                const float2 vE = df::vsub(e1, w1), vN = df::vsub(n1, s1);
-                const float2 vNE = df::vsub(ne, sw), vSE = df::vsub(se, nw);
-                const float dE = vE.x + vE.y, dN = vN.x + vN.y, dNE = vNE.x + vNE.y, dSE = vSE.x + vSE.y;
-                // grad X = 3 sum_pairs w e (X(r+e) - X(r-e)): faces 1/9, diagonals 1/36;
-                // lanes (d/dx, d/dy)
-                const float2 g = df::vmul(df::vbc(3.0f),
-                                          df::vfma(df::vbc(1.0f / 9.0f), make_float2(dE, dN),
-                                                   df::vmul(df::vbc(1.0f / 36.0f),
-                                                            df::vadd(df::vbc(dNE), make_float2(dSE, -dSE)))));
-                G[i * N + ob] = g;
+                const float dE = (e1.x - w1.x) + (e1.y - w1.y);
+                const float dN = (n1.x - s1.x) + (n1.y - s1.y);
+                const float dNE = (ne.x - sw.x) + (ne.y - sw.y);
+                const float dSE = (se.x - nw.x) + (se.y - nw.y);
+                // grad X = 3 sum_pairs w e (X(r+e) - X(r-e)): faces 1/9, diagonals 1/36
+                const float gx = 3.0f * fmaf(1.0f / 9.0f, dE, (1.0f / 36.0f) * (dNE + dSE));
+                const float gy = 3.0f * fmaf(1.0f / 9.0f, dN, (1.0f / 36.0f) * (dNE - dSE));
+                G[i * N + ob] = make_float2(gx, gy);
             }
         }
     }

@@ -213,27 +213,16 @@ __device__ __forceinline__ void psi_and_B(const Params &P, const float (&h)[NC],
     B = fast_two_sum(t.s.y, t.c.y);
 }
 
-__device__ __forceinline__ F2x2 mul_u2(F2x2 a, F2x2 b)
-{
-    const F2x2 p = two_prod2(a.hi, b.hi);
-    return {p.hi, vfma(a.hi, b.lo, vfma(a.lo, b.hi, p.lo))};
-}
-__device__ __forceinline__ F2x2 bc2(F2 a) { return {vbc(a.hi), vbc(a.lo)}; }
-__device__ __forceinline__ F2x2 lanes(float4 v) { return {make_float2(v.x, v.y), make_float2(v.z, v.w)}; }
-__device__ __forceinline__ F2x2 neg2(F2x2 a) { return {vneg(a.hi), vneg(a.lo)}; }
 
 // mu of one node with rolled loops over the row pairs of T_i and over the
 // components (the unrolled form above is a few thousand instructions of
 // straight-line code at Nc = 10, more than the instruction cache holds).
-// Components 2q and 2q+1 go through one iteration on the packed FP32x2
-// units, each lane with the operations of mu(), so the result is bitwise
+// The same operations in the same order as mu(), so the result is bitwise
 // that of mu().  B (Eq. 11, from mix_B or psi_and_B) comes in.  Per-thread
 // scratch in shared memory with stride `pitch`: PH, PL [NC] floats (the
-// density pair) and TS [NC] float2 holding T_i, with the pair q stored as
-// TS[2q] = (hi_2q, hi_2q+1), TS[2q+1] = (lo_2q, lo_2q+1) and an odd last
-// component as (hi, lo).  mu_i is written to out[i * ostride]; TS may be
-// out itself (same stride): iteration q reads T_2q, T_2q+1 before it stores
-// their mu.  Tab: a view of the log table (lbm_df64.cuh).
+// density pair) and TS [NC] float2 (T_i as (hi, lo)); mu_i is written to
+// out[i * ostride].  TS may be out itself (same stride): iteration i reads
+// T_i before it stores mu_i.  Tab: a view of the log table (lbm_df64.cuh).
 template <int NC, typename Tab>
 __device__ __forceinline__ void mu_rolled(const Params &P, Tab tab, const float (&h)[NC], const float (&l)[NC],
                                           F2 B, F2 lap, float *PH, float *PL, float2 *TS, int pitch, float2 *out,
@@ -261,9 +250,9 @@ __device__ __forceinline__ void mu_rolled(const Params &P, Tab tab, const float 
         t.first(P.dAp[r * kMaxNc], h[0], l[0]);
 #pragma unroll
         for (int j = 1; j < NC; ++j) t.add(P.dAp[r * kMaxNc + j], h[j], l[j]);
-        const F2x2 v = fast_two_sum2(t.s, t.c);  // fast_two_sum lane by lane
-        TS[(2 * r) * pitch] = v.hi;
-        TS[(2 * r + 1) * pitch] = v.lo;
+        const F2 a = fast_two_sum(t.s.x, t.c.x), b = fast_two_sum(t.s.y, t.c.y);
+        TS[(2 * r) * pitch] = make_float2(a.hi, a.lo);
+        TS[(2 * r + 1) * pitch] = make_float2(b.hi, b.lo);
     }
     if constexpr (NC % 2 == 1) {
         DotPos t;
@@ -273,12 +262,7 @@ __device__ __forceinline__ void mu_rolled(const Params &P, Tab tab, const float 
         const F2 v = t.value();
         TS[(NC - 1) * pitch] = make_float2(v.hi, v.lo);
     }
-    // T_i in the layout above
-    auto Ti = [&](int i) -> F2 {
-        if (NC % 2 == 1 && i == NC - 1) return f2(TS[i * pitch]);
-        const float2 a = TS[(i & ~1) * pitch], b = TS[((i & ~1) + 1) * pitch];
-        return (i & 1) ? F2{a.y, b.y} : F2{a.x, b.x};
-    };
+    auto Ti = [&](int i) -> F2 { return f2(TS[i * pitch]); };
     DotPos qd;
     qd.first(y[0], Ti(0));
 #pragma unroll
@@ -298,25 +282,8 @@ __device__ __forceinline__ void mu_rolled(const Params &P, Tab tab, const float 
                        mul(mul(Q, u), add(mul(Lu, {hi_of(0.5 / kS2), lo_of(0.5 / kS2)}), neg(w))));
     const F2 RC2 = mul(Lu, {hi_of(-1.0 / kS2), lo_of(-1.0 / kS2)});
     const F2 RG = mul(RT, lnomB);
-    const F2x2 RT2 = bc2(RT), nRG2 = bc2(neg(RG)), RC12 = bc2(RC1), RC22 = bc2(RC2), lap2 = bc2(lap);
 #pragma unroll 1
-    for (int q = 0; q < NC / 2; ++q) {
-        const F2x2 x = {make_float2(PH[(2 * q) * pitch], PH[(2 * q + 1) * pitch]),
-                        make_float2(PL[(2 * q) * pitch], PL[(2 * q + 1) * pitch])};
-        const F2x2 T = {TS[(2 * q) * pitch], TS[(2 * q + 1) * pitch]};
-        Dot2 a;
-        a.start(mul_u2(RT2, log2x(x, tab)));
-        a.add_term(lanes(P.dRKp[q]));
-        a.add_term(nRG2);
-        a.add_term(mul_u2(lanes(P.dbp[q]), RC12));
-        a.add_term(mul_u2(T, RC22));
-        a.add_term(neg2(mul_u2(lanes(P.dsqkp[q]), lap2)));
-        const F2x2 m = a.value();
-        out[(long long)(2 * q) * ostride] = make_float2(m.hi.x, m.lo.x);
-        out[(long long)(2 * q + 1) * ostride] = make_float2(m.hi.y, m.lo.y);
-    }
-    if constexpr (NC % 2 == 1) {
-        constexpr int i = NC - 1;
+    for (int i = 0; i < NC; ++i) {
         Dot a;
         const F2 t0 = mul_u(RT, log({PH[i * pitch], PL[i * pitch]}, tab));
         a.s = t0.hi;
@@ -324,7 +291,7 @@ __device__ __forceinline__ void mu_rolled(const Params &P, Tab tab, const float 
         a.add_term(f2(P.dRK[i]));
         a.add_term(neg(RG));
         a.add_term(mul_u(f2(P.db[i]), RC1));
-        a.add_term(mul_u(f2(TS[i * pitch]), RC2));
+        a.add_term(mul_u(Ti(i), RC2));
         a.add_term(neg(mul_u(f2(P.dsqk[i]), lap)));
         const F2 m = a.value();
         out[(long long)i * ostride] = make_float2(m.hi, m.lo);
