@@ -11,6 +11,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -474,27 +475,41 @@ int finish_init(lbm_problem *p)
 }
 
 // Host validation of the initial fields, branch-free within blocks of 4096
-// values so that the compiler can vectorise it.
+// values so that the compiler can vectorise it; large fields are split over
+// up to eight host threads.
+template <typename Pred> bool all_of_blocks(const double *x, size_t n, Pred ok)
+{
+    auto range = [&](size_t lo, size_t hi) {
+        for (size_t b = lo; b < hi; b += 4096) {
+            const size_t e = std::min(hi, b + 4096);
+            int bad = 0;
+            for (size_t k = b; k < e; ++k) bad |= !ok(x[k]);
+            if (bad) return false;
+        }
+        return true;
+    };
+    const unsigned hw = std::thread::hardware_concurrency();
+    const unsigned nt = n < ((size_t)1 << 22) ? 1u : std::max(1u, std::min(8u, hw));
+    if (nt == 1) return range(0, n);
+    std::vector<std::thread> th;
+    std::vector<char> res(nt, 1);
+    const size_t chunk = (n + nt - 1) / nt;
+    for (unsigned t = 0; t < nt; ++t)
+        th.emplace_back([&, t] { res[t] = range(std::min(n, t * chunk), std::min(n, (t + 1) * chunk)); });
+    for (auto &x_ : th) x_.join();
+    for (char r : res)
+        if (!r) return false;
+    return true;
+}
+
 bool all_positive_finite(const double *x, size_t n)
 {
-    for (size_t b = 0; b < n; b += 4096) {
-        const size_t e = std::min(n, b + 4096);
-        int bad = 0;
-        for (size_t k = b; k < e; ++k) bad |= !(x[k] > 0.0 && x[k] <= 1.7976931348623157e308);
-        if (bad) return false;
-    }
-    return true;
+    return all_of_blocks(x, n, [](double v) { return v > 0.0 && v <= 1.7976931348623157e308; });
 }
 
 bool all_finite(const double *x, size_t n)
 {
-    for (size_t b = 0; b < n; b += 4096) {
-        const size_t e = std::min(n, b + 4096);
-        int bad = 0;
-        for (size_t k = b; k < e; ++k) bad |= !(x[k] >= -1.7976931348623157e308 && x[k] <= 1.7976931348623157e308);
-        if (bad) return false;
-    }
-    return true;
+    return all_of_blocks(x, n, [](double v) { return v >= -1.7976931348623157e308 && v <= 1.7976931348623157e308; });
 }
 
 int check_flag(lbm_problem *p)

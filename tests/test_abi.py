@@ -133,3 +133,17 @@ def test_timing_arguments_and_states(lib):
     p.timing_enable(False)
     assert lib._lib.lbm_timing_read(p._h, buf, 4, ctypes.byref(n)) == lib.LBM_ESTATE
     p.close()
+
+
+def test_init_fields_rejects_bad_values_in_large_fields(lib):
+    """The host validation of lbm_init_fields splits large fields over host
+    threads; a bad value in any part is still rejected before any device work."""
+    nx = ny = 2048  # 4,194,304 values: the threaded path
+    p = lib.Problem(0, nx, ny, 1, [0.04], [0.1], [0.1], None, 0.06, 1.0)
+    rho = np.full(nx * ny, 0.5)
+    for k in (0, nx * ny // 3, nx * ny - 1):
+        bad = rho.copy()
+        bad[k] = -1.0 if k % 2 == 0 else float("nan")
+        st = lib._lib.lbm_init_fields(p._h, bad.ctypes.data_as(lib._dp), None)
+        assert st == lib.LBM_EINVAL, (k, st)
+    p.close()
