@@ -364,8 +364,9 @@ constexpr int kWmax32 = kT - 6;  // binary32 kernel: one density column per thre
 // pass before the step kernel.  Each CTA walks a segment of rows of a strip
 // of W <= kT - 4 columns; for row k it forms
 //   psi(k) (Eq. 4) on columns [-2, W + 1] from the state's exact density pairs,
+//     with B(k) = b_m rho~ (Eq. 11) in the same packed sum,
 //   mu(k-1) (Eqs. 5, 9-12 through lbm_thermo_df.cuh) on columns [-1, W] from
-//     psi rows k-2..k and the pairs of row k-1 kept from the previous row,
+//     psi rows k-2..k and the pairs and B of row k-1 kept from the previous row,
 //   grad mu(k-2) on the interior columns from mu rows k-3..k-1, every
 //     difference mu(r + e) - mu(r - e) taken on the (hi, lo) pairs and
 //     rounded once (so it carries the df64 accuracy of mu), written to
