@@ -522,27 +522,22 @@ def ulp32(x):
 
 def tie_line_errors(d, jobs, states, sample):
     """Largest relative deviation of each sampled converged slab's vapour and
-    liquid mole fractions (x = 0 and x = nx/2) from the oracle flash at the
-    slab's own pressure (Eq. 9 at the two centres) and conserved composition."""
-    from oracle import OracleProblem
-    from oracle.thermo import flash
+    liquid mole fractions (x = 0 and x = nx/2) from the flash compositions
+    stored with the slab (the flash at its initial T, p and z, written by
+    oracle/make_workloads.py).  The slab's pressure settles slightly away from
+    the initial one, so this includes that drift; the tests compare with the
+    flash at the slab's own pressure."""
     errs = []
     for k in sample:
-        T, rho = jobs[k]
         st = states[k]
         if not st["converged"]:
             continue
-        P = OracleProblem(0, 1, 1, 1, d["a"], d["b"], d["omega"], np.asarray(d["kij"]), T=T,
-                          kappa_ref=d["kappa_ref"])
         rm = st["rho"][:, 0]
         nx = rm.shape[1]
         rV, rL = rm[:, 0], rm[:, nx // 2]
-        p = 0.5 * (P.eos(rV)[0] + P.eos(rL)[0])
-        tot = rm.sum(axis=1)
-        fl = flash(P, p, tot / tot.sum())
-        if fl is None:
-            continue
-        errs.append(max(np.abs((rV / rV.sum()) / fl.y - 1).max(), np.abs((rL / rL.sum()) / fl.x - 1).max()))
+        job = d["jobs"][k]
+        y, x = np.asarray(job["y"]), np.asarray(job["x"])
+        errs.append(max(np.abs((rV / rV.sum()) / y - 1).max(), np.abs((rL / rL.sum()) / x - 1).max()))
     return errs
 
 
@@ -607,7 +602,8 @@ def run_batched(args, lbmfug, local):
             "rounds": info["rounds"], "precision": "fp32 (binary32 state and thermodynamics)",
             "unconverged_last_drho": sorted(float(states[k]["last_drho"]) for k in unconv)[-5:],
             "tie_line_vs_flash": {"slabs": len(errs), "max_rel": float(max(errs)) if errs else None,
-                                  "median_rel": float(np.median(errs)) if errs else None},
+                                  "median_rel": float(np.median(errs)) if errs else None,
+                                  "against": "the stored flash at each slab's initial (T, p, z)"},
             "fp64_one_at_a_time": {"measured": True, "solves": s64, "wall_s": w64,
                                    "solves_per_s": s64 / w64 if w64 > 0 else None,
                                    "node_steps_per_s": ns64 / w64 if w64 > 0 else None,
